@@ -1,0 +1,440 @@
+#!/usr/bin/env python3
+"""F / F* matvec throughput on the paper-shaped operator, one JSON line.
+
+Workload: the paper-shaped single operator, Nt=1000, Nd=100, Nm=10000
+(F-hat is 1001 x 100 x 10000 complex), block entries N(0,1) scaled by
+exp(-k/200) over the lag k, one right-hand side m ~ N(0,1) for F and one
+d ~ N(0,1) for F*.  A step is one F matvec and one F* matvec (every phase of
+Section 2.4: pad, FFT, block matvec, IFFT, unpad), so a step is 2 matvecs.
+
+value      matvecs/s over all ranks with inputs resident in HBM, device time
+           from CUDA events on the launching stream; the headline precision
+           is all-FP64-class (every phase FP64, the block matvec in the
+           double-float FP32 hi/lo mode, relative L2 <= 1e-12 to the oracle).
+e2e        the same metric through the public API with host (pinned) buffers,
+           host<->device copies inside the timed region.
+roofline   the block-matvec kernels (about 90 % of a step): algorithmic bytes
+           per launch (F-hat at its stored width + input + output vectors of
+           one matvec) over their mean CUDA-event duration, against the
+           measured HBM copy bandwidth.
+variants   the plain FP64 path (native FP64 FMA), the paper's mixed-precision
+           optimum, all-FP32, each with matvecs/s and sampled error.
+cpu_baseline  the CPU oracle's FFT path on a column sample, scaled.
+
+--impl reference runs the CPU oracle itself (the only reference there is) on a
+bounded column sample of the same workload and prints the same line.
+Multi-GPU (torchrun): every rank runs its own operator (no collective on the
+data path), value = all matvecs / max-over-ranks time, scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NT, ND, NM = 1000, 100, 10000
+DECAY = 200.0
+METRIC = "F/F* matvec/s & HBM-roofline frac, Nt=1000 Nd=100 Nm=1e4; served p50/p99 ms"
+UNIT = "matvec/s"
+WORKLOAD = "paper-shaped single operator Nt=1000 Nd=100 Nm=10000, F and F* matvec, 1 RHS"
+HEADLINE = ("ddddd", "f64x2f32")
+VARIANTS = {
+    "fp64_native": (("ddddd", "native"), ("ddddd", "native")),
+    "fp64_class_hilo": (("ddddd", "f64x2f32"), ("ddddd", "f64x2f32")),
+    "paper_mp_optimum": (("dssdd", "native"), ("ddssd", "native")),
+    "all_fp32": (("sssss", "native"), ("sssss", "native")),
+}
+KERNELS_PER_MATVEC = 3
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--Nt", type=int, default=NT)
+    p.add_argument("--Nd", type=int, default=ND)
+    p.add_argument("--Nm", type=int, default=NM)
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# helpers shared with the multi-process tests
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over all ranks (x itself when there is one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int, device=None) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def algorithmic_bytes(Nt: int, Nd: int, Nm: int, fhat_entry_bytes: int, io_bytes: int = 8) -> int:
+    """Bytes one matvec must move: F-hat at its stored width plus the input and
+    output vectors (Nf = Nt + 1 frequencies of the paper's 2 Nt padding)."""
+    Nf = Nt + 1
+    return Nf * Nd * Nm * fhat_entry_bytes + Nt * Nm * io_bytes + Nt * Nd * io_bytes
+
+
+def fhat_entry_bytes(prec: str, mode: str) -> int:
+    return 8 if prec[2] == "s" else 16
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            if self.uuid and self.uuid not in f[0]:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.REASONS, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return max(n) if n else 1
+    except Exception:
+        return len(os.sched_getaffinity(0))
+
+
+class OracleSample:
+    """The oracle's FFT path on the first Nm_s columns of the operator."""
+
+    def __init__(self, Fcol, m, d, Nm_s: int):
+        import oracle
+        self.oracle = oracle
+        self.Nt = Fcol.shape[0]
+        self.Nm_full = Fcol.shape[2]
+        self.Nm_s = Nm_s
+        self.Fh = oracle.spectrum(Fcol[:, :, :Nm_s])
+        self.m = m[:, :Nm_s].copy()
+        self.d = d.copy()
+
+    def step(self):
+        self.oracle.matvec_fft_spec(self.Fh, self.m, self.Nt)
+        self.oracle.rmatvec_fft_spec(self.Fh, self.d, self.Nt)
+
+    def time_steps(self, n: int) -> float:
+        t0 = time.perf_counter()
+        for _ in range(n):
+            self.step()
+        return time.perf_counter() - t0
+
+    def describe(self) -> str:
+        return (f"oracle FFT path (scipy.fft + numpy matmul, FP64) on columns 0..{self.Nm_s - 1} of the "
+                f"Nm={self.Nm_full} operator (F-hat {self.Fh.nbytes / 1e9:.2f} GB), F + F* per step; "
+                f"matvec/s scaled by {self.Nm_s}/{self.Nm_full} (work is linear in Nm)")
+
+
+def cpu_baseline(Fcol, m, d, budget_s: float = 15.0) -> dict:
+    samp = OracleSample(Fcol, m, d, Nm_s=min(1000, Fcol.shape[2]))
+    samp.step()
+    t1 = samp.time_steps(1)
+    n = max(1, int(budget_s / max(t1, 1e-3)))
+    t = samp.time_steps(n)
+    rate = 2 * n / t * samp.Nm_s / samp.Nm_full
+    return {"value": rate, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+            "sample": samp.describe() + f"; {n} steps in {t:.1f} s"}
+
+
+def run_reference(args) -> None:
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    import synth
+    Nt, Nd, Nm = args.Nt, args.Nd, args.Nm
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=0, decay=DECAY)
+    m = synth.vectors(synth.TAG_M, Nt, Nm, seed=0)[0]
+    d = synth.vectors(synth.TAG_D, Nt, Nd, seed=0)[0]
+    Nm_s = min(1000, Nm)
+    samp = OracleSample(Fcol, m, d, Nm_s)
+    t1 = samp.time_steps(1)
+    total = (args.steps + args.warmup) * t1
+    if total > 150.0:  # keep the whole run within a few minutes
+        Nm_s = max(8, int(Nm_s * 150.0 / total))
+        samp = OracleSample(Fcol, m, d, Nm_s)
+    samp.time_steps(args.warmup)
+    t = samp.time_steps(args.steps)
+    value = 2 * args.steps / t * Nm_s / Nm
+    cores = _blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps * Nm / Nm_s,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "Nt": Nt, "Nd": Nd, "Nm": Nm},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": samp.describe()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def sampled_error(Fcol, m, d, y, x, n=24, seed=123) -> tuple[float, float]:
+    """Relative L2 error of sampled outputs against the oracle's definition."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    Nt, Nd, Nm = Fcol.shape
+    idx = [(int(rng.integers(Nt)), int(rng.integers(Nd))) for _ in range(n)]
+    ref = oracle.matvec_entries(Fcol, m, idx)
+    got = np.array([y[i, r] for i, r in idx])
+    e1 = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    idx = [(int(rng.integers(Nt)), int(rng.integers(Nm))) for _ in range(n)]
+    ref = oracle.rmatvec_entries(Fcol, d, idx)
+    got = np.array([x[j, c] for j, c in idx])
+    e2 = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return e1, e2
+
+
+def time_variant(torch, op, mt, dt, yt, xt, stream, pf, pa, steps: int) -> dict:
+    op.set_precision("F", *pf)
+    op.set_precision("F*", *pa)
+    for _ in range(3):
+        op.matvec(mt, out=yt, stream=stream)
+        op.rmatvec(dt, out=xt, stream=stream)
+    torch.cuda.synchronize()
+    op.reset_timing()
+    op.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        op.matvec(mt, out=yt, stream=stream)
+        op.rmatvec(dt, out=xt, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    op.set_timing(False)
+    ms = e0.elapsed_time(e1)
+    tf, nf = op.phase_times("F")
+    ta, na = op.phase_times("F*")
+    return {"ms_step": ms / steps, "matvec_s": 2 * steps / (ms * 1e-3),
+            "gemv_ms_F": tf[1] / nf, "gemv_ms_Fstar": ta[1] / na,
+            "phase_ms_F": [v / nf for v in tf], "phase_ms_Fstar": [v / na for v in ta]}
+
+
+def main(args) -> None:
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2508_10202_gb300 import Operator
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    Nt, Nd, Nm = args.Nt, args.Nd, args.Nm
+    seed = rank
+
+    t0 = time.perf_counter()
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=seed, decay=DECAY)
+    m = synth.vectors(synth.TAG_M, Nt, Nm, seed=seed)[0]
+    d = synth.vectors(synth.TAG_D, Nt, Nd, seed=seed)[0]
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    op = Operator(Fcol)                      # host block column: staged setup FFT in FP64
+    t_setup = time.perf_counter() - t0
+
+    stream = torch.cuda.current_stream(dev)
+    mt = torch.from_numpy(m).to(dev)
+    dt = torch.from_numpy(d).to(dev)
+    yt = torch.empty((Nt, Nd), dtype=torch.float64, device=dev)
+    xt = torch.empty((Nt, Nm), dtype=torch.float64, device=dev)
+
+    # --- headline: timed region, max over ranks --------------------------------
+    op.set_precision("F", *HEADLINE)
+    op.set_precision("F*", *HEADLINE)
+    for _ in range(args.warmup):
+        op.matvec(mt, out=yt, stream=stream)
+        op.rmatvec(dt, out=xt, stream=stream)
+    op.set_timing(True)
+    op.reset_timing()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        op.matvec(mt, out=yt, stream=stream)
+        op.rmatvec(dt, out=xt, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world, dev)
+    units = sum_over_ranks(2.0 * args.steps, world, dev)
+    value = units / (ms_max * 1e-3)
+    tf, nf = op.phase_times("F")
+    ta, na = op.phase_times("F*")
+    op.set_timing(False)
+    y = yt.cpu().numpy()
+    x = xt.cpu().numpy()
+    err_f, err_a = sampled_error(Fcol, m, d, y, x)
+
+    # --- roofline of the block-matvec kernels ----------------------------------
+    peak, peak_kind = load_peaks()
+    ab = algorithmic_bytes(Nt, Nd, Nm, fhat_entry_bytes(*HEADLINE))
+    gemv_ms = (tf[1] + ta[1]) / (nf + na)
+    achieved = ab / (gemv_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "gemv_n_kernel<KindDF> (F) / gemv_h_kernel<KindDF> (F*)",
+                "bytes_per_launch": ab, "gemv_ms_F": tf[1] / nf, "gemv_ms_Fstar": ta[1] / na,
+                "frac_F": ab / (tf[1] / nf * 1e-3) / 1e9 / peak, "frac_Fstar": ab / (ta[1] / na * 1e-3) / 1e9 / peak,
+                "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "phase_ms_F": [v / nf for v in tf], "phase_ms_Fstar": [v / na for v in ta]}
+
+    # --- end to end through the public API with host buffers -------------------
+    mh = torch.from_numpy(m).pin_memory()
+    dh = torch.from_numpy(d).pin_memory()
+    yh = torch.empty((Nt, Nd), dtype=torch.float64).pin_memory()
+    xh = torch.empty((Nt, Nm), dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        op.matvec(mh, out=yh)
+        op.rmatvec(dh, out=xh)
+    e2e_steps = max(10, min(args.steps, 100))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        op.matvec(mh, out=yh)
+        op.rmatvec(dh, out=xh)
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(t_e2e, world, dev)
+    e2e = {"value": sum_over_ranks(2.0 * e2e_steps, world, dev) / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(m.nbytes + d.nbytes), "d2h_bytes_per_step": int(y.nbytes + x.nbytes),
+           "steps": e2e_steps}
+
+    # --- variants (rank 0 only) --------------------------------------------------
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        for name, (pf, pa) in VARIANTS.items():
+            r = time_variant(torch, op, mt, dt, yt, xt, stream, pf, pa, steps=max(20, args.steps // 5))
+            ef, ea = sampled_error(Fcol, m, d, yt.cpu().numpy(), xt.cpu().numpy())
+            abv = algorithmic_bytes(Nt, Nd, Nm, fhat_entry_bytes(*pf))
+            r.update({"prec_F": "/".join(pf), "prec_Fstar": "/".join(pa), "rel_err_F": ef, "rel_err_Fstar": ea,
+                      "gemv_frac_F": abv / (r["gemv_ms_F"] * 1e-3) / 1e9 / peak,
+                      "gemv_frac_Fstar": abv / (r["gemv_ms_Fstar"] * 1e-3) / 1e9 / peak})
+            variants[name] = r
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(Fcol, m, d)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2 (FP64-class double-float; FP64 FFTs)",
+            "data": "synthetic (seeded N(0,1) blocks x exp(-k/200), N(0,1) vectors)",
+            "config": {"workload": WORKLOAD, "Nt": Nt, "Nd": Nd, "Nm": Nm, "rhs": 1,
+                       "precision": "ddddd / block matvec f64x2f32", "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2: F-hat is 16 GB per matvec, read once"},
+            "gpu_launches": KERNELS_PER_MATVEC * 2 * args.steps,
+            "rel_err": {"F": err_f, "Fstar": err_a, "how": "24 sampled outputs vs the oracle's definition"},
+            "roofline": roofline, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "variants": variants,
+            "setup_s": t_setup, "gen_s": t_gen,
+        }
+        print(json.dumps(line), flush=True)
+    op.free()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        main(a)

@@ -1,0 +1,160 @@
+/*
+ * fftmv.h - C ABI of the GB300 block-Toeplitz matvec library (libfftmv.so).
+ *
+ * Computes d = F m and m = F* d for a block lower-triangular Toeplitz matrix F
+ * with Nt x Nt blocks of size Nd x Nm (Section 2.3 of Venkat et al.,
+ * "Mixed-Precision Performance Portability of FFT-Based GPU-Accelerated
+ * Algorithms for Block-Triangular Toeplitz Matrices", Eq. (ShiftInvariance)):
+ *
+ *     d_i  = sum_{j <= i} F_{i-j} m_j          (F,  i = 0..Nt-1)
+ *     m*_j = sum_{i >= j} F_{i-j}^T d_i        (F*, j = 0..Nt-1)
+ *
+ * by the five-phase FFT algorithm of Section 2.4: zero pad in time, batched
+ * real FFT, per-frequency complex block matvec against F-hat (F-hat^H for F*),
+ * inverse FFT, unpad.  Every phase runs in hand-written sm_103a kernels on one
+ * GPU; per-phase FP32/FP64 precision follows Section 3.2.
+ *
+ * Layout.  Every array is row-major, time outer and space inner (the blocks
+ * of Section 2.3 laid end to end):
+ *     block column  F_col[k][r][n]      k < Nt, r < Nd, n < Nm   (FP64)
+ *     parameters    m[b][j][n]          b < K right-hand sides
+ *     data          d[b][i][r]
+ * Right-hand sides are contiguous and outermost.
+ *
+ * Ownership.  The operator owns F-hat in every stored form and its own
+ * scratch; the caller owns F_col, m and d.  Pointers may be device pointers
+ * (including managed memory) or host pointers; the library asks the CUDA
+ * runtime which.  Device I/O is stream ordered and asynchronous: the caller
+ * keeps the buffers alive until the stream has run the work.  Host I/O is
+ * staged through device memory and the call returns after the result has
+ * reached host memory.
+ *
+ * Errors.  Every entry point returns an fftmv_status.  Nothing aborts, traps
+ * or throws across the ABI.  On failure fftmv_last_error() returns a message
+ * for the calling thread.  Arguments are checked before any work is queued.
+ *
+ * Threads and streams.  Different operators may be used from different
+ * threads at once.  Calls on one operator may run on different streams at the
+ * same time (each call takes its scratch from a stream-ordered pool), except
+ * that fftmv_set_precision and fftmv_free must not overlap other calls on the
+ * same operator.
+ */
+#ifndef FFTMV_H
+#define FFTMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fftmv_op fftmv_op; /* opaque operator handle */
+
+typedef enum {
+  FFTMV_OK = 0,
+  FFTMV_EINVAL = -1,       /* bad argument: null pointer, size, enum value */
+  FFTMV_ENOMEM = -2,       /* device or host allocation failed */
+  FFTMV_EUNSUPPORTED = -3, /* valid but not supported (e.g. time length too long) */
+  FFTMV_ECUDA = -4,        /* a CUDA call failed; see fftmv_last_error() */
+  FFTMV_ESTATE = -5        /* operator in the wrong state (e.g. freed) */
+} fftmv_status;
+
+/* Precision of one phase (Section 3.2): each phase runs in FP32 or FP64. */
+typedef enum { FFTMV_F64 = 0, FFTMV_F32 = 1 } fftmv_phase_prec;
+
+/* How phase 3 (the per-frequency block matvec) stores F-hat and computes.
+ *   NATIVE   : gemv=F64 -> F-hat FP64 (16 B/entry), FP64 FMA.
+ *              gemv=F32 -> F-hat FP32 (8 B/entry), FP32 FMA.
+ *   F64X2F32 : gemv=F64 only.  F-hat as FP32 hi+lo pairs (16 B/entry, about
+ *              48 significant bits), double-float arithmetic on the FP32
+ *              pipe.  Not native FP64: an FP64-class emulation for GPUs whose
+ *              FP64 rate cannot keep pace with memory (GB300). */
+typedef enum { FFTMV_GEMV_NATIVE = 0, FFTMV_GEMV_F64X2F32 = 1 } fftmv_gemv_mode;
+
+/* Per-phase precisions, in the execution order of the operation they are set
+ * for (for F*: pad and FFT act on d, IFFT and unpad on the output m). */
+typedef struct {
+  int32_t pad;       /* fftmv_phase_prec: phase 1, zero padding (input cast)   */
+  int32_t fft;       /* phase 2, forward FFT                                    */
+  int32_t gemv;      /* phase 3, block matvec; also the stored F-hat precision  */
+  int32_t ifft;      /* phase 4, inverse FFT                                    */
+  int32_t unpad;     /* phase 5, unpadding (output cast)                        */
+  int32_t gemv_mode; /* fftmv_gemv_mode                                         */
+} fftmv_precision;
+
+typedef enum { FFTMV_FORWARD = 0 /* F */, FFTMV_ADJOINT = 1 /* F* */ } fftmv_which;
+typedef enum { FFTMV_IO_F64 = 0, FFTMV_IO_F32 = 1 } fftmv_io_dtype;
+
+typedef struct {
+  int64_t Nt, Nd, Nm; /* block sizes */
+  int64_t L;          /* FFT length: the smallest even 2^a 3^b 5^c >= 2 Nt - 1 */
+  int64_t Nf;         /* frequencies kept: L / 2 + 1 */
+  int64_t ldn;        /* stored row length of F-hat: Nm rounded up to 8 */
+  int32_t device;     /* CUDA device the operator lives on */
+  size_t fhat_bytes;  /* device bytes held by F-hat in all stored forms */
+} fftmv_info;
+
+/* Build the operator from its first block column (Section 2.4: only the first
+ * block column is stored; it is zero padded to length L and Fourier
+ * transformed once, always in FP64, Section 3.2).
+ *   F_col  : Nt*Nd*Nm doubles, [k][r][n] row-major, host or device memory;
+ *            read during the call only.
+ *   Nt, Nd, Nm >= 1.  Nt is limited by the shared-memory FFT (L <= 7264;
+ *            EUNSUPPORTED beyond).
+ *   stream : cudaStream_t used for the setup work (NULL = legacy default).
+ *   out    : receives the new handle.
+ * Creates on the current CUDA device.  Synchronous: returns after F-hat is
+ * built.  Both F and F* start in all-FP64 precision, gemv_mode NATIVE. */
+int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t Nm, void* stream,
+                          fftmv_op** out);
+
+/* Set the per-phase precisions used by later calls for F (which=FORWARD) or
+ * F* (which=ADJOINT) (Section 3.2: set at creation, changeable at runtime).
+ * Builds the stored F-hat form the GEMV phase needs if it does not exist yet
+ * (synchronously).  EINVAL for out-of-range values or F64X2F32 with an FP32
+ * GEMV phase. */
+int fftmv_set_precision(fftmv_op* op, int which, const fftmv_precision* prec);
+int fftmv_get_precision(const fftmv_op* op, int which, fftmv_precision* out);
+
+/* d = F m for K right-hand sides (Section 2.4, phases 1-5).
+ *   m : K*Nt*Nm values [b][j][n]; d : K*Nt*Nd values [b][i][r].
+ *   io_dtype : FFTMV_IO_F64 or FFTMV_IO_F32 for both m and d.
+ *   K >= 0 (K = 0 does nothing).  m and d must not overlap. */
+int fftmv_matvec(fftmv_op* op, const void* m, void* d, int64_t K, int io_dtype, void* stream);
+
+/* m = F* d for K right-hand sides: the same phases with the conjugate
+ * transpose block matvec, input and output swapped (Section 2.4).
+ *   d : K*Nt*Nd values; m : K*Nt*Nm values. */
+int fftmv_rmatvec(fftmv_op* op, const void* d, void* m, int64_t K, int io_dtype, void* stream);
+
+/* Device scratch one call takes from the operator's stream-ordered pool
+ * (which = FORWARD or ADJOINT), not counting host-I/O staging. */
+int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out);
+
+int fftmv_get_info(const fftmv_op* op, fftmv_info* out);
+
+/* Per-phase CUDA-event timers (the paper's per-phase timings).  While
+ * enabled, every call records events on its stream around its three kernel
+ * groups: [0] pad+FFT, [1] block matvec, [2] IFFT+unpad.  fftmv_phase_times
+ * waits for the recorded events and returns the summed milliseconds and the
+ * number of calls for F or F*; reset clears them. */
+int fftmv_set_timing(fftmv_op* op, int enable);
+int fftmv_phase_times(fftmv_op* op, int which, double ms_out[3], int64_t* calls_out);
+int fftmv_reset_timing(fftmv_op* op);
+
+/* Release every device resource of the operator.  NULL is a no-op.  Waits
+ * for the operator's pending work. */
+int fftmv_free(fftmv_op* op);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char* fftmv_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int fftmv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTMV_H */

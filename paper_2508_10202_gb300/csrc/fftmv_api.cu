@@ -1,0 +1,566 @@
+// C ABI of the block-Toeplitz matvec library: operator object, argument
+// checks, scratch from a stream-ordered pool, and the phase sequence of
+// Section 2.4 (pad+FFT, block matvec, IFFT+unpad) with the per-phase
+// precisions of Section 3.2.  See include/fftmv.h for the contract.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "fftmv.h"
+#include "fftmv_internal.h"
+
+using namespace fftmv;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky-free error so later calls can proceed
+  return fail(e == cudaErrorMemoryAllocation ? FFTMV_ENOMEM : FFTMV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+std::mutex g_reg_mu;
+std::set<const fftmv_op*> g_live;
+
+bool smooth235(int64_t n) {
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+// smallest even 2^a 3^b 5^c >= 2 Nt - 1: no circular wrap reaches outputs t < Nt
+int64_t choose_length(int64_t Nt) {
+  int64_t L = 2 * Nt - 1;
+  if (L < 2) L = 2;
+  if (L % 2) ++L;
+  while (!smooth235(L)) L += 2;
+  return L;
+}
+
+FftPlan make_plan(int64_t L) {
+  FftPlan p{};
+  p.L = (int)L;
+  int64_t n = L;
+  int np = 0;
+  while (n % 8 == 0) { p.rad[np++] = 8; n /= 8; }
+  while (n % 4 == 0) { p.rad[np++] = 4; n /= 4; }
+  while (n % 2 == 0) { p.rad[np++] = 2; n /= 2; }
+  while (n % 5 == 0) { p.rad[np++] = 5; n /= 5; }
+  while (n % 3 == 0) { p.rad[np++] = 3; n /= 3; }
+  p.npass = np;
+  return p;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct TimingSet {
+  cudaEvent_t ev[4];
+  int which;
+};
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct fftmv_op {
+  int device = 0;
+  int64_t Nt = 0, Nd = 0, Nm = 0, L = 0, Nf = 0, ldn = 0;
+  FftPlan plan{};
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  double2* fhat64 = nullptr;  // master F-hat [Nf][Nd][ldn], FP64
+  float4* fhat_df = nullptr;  // FP32 hi/lo pairs
+  float2* fhat32 = nullptr;   // FP32
+  fftmv_precision prec[2]{};
+  cudaMemPool_t pool = nullptr;
+  std::mutex mu;  // timing state
+  bool timing = false;
+  std::vector<TimingSet> free_sets, pending;
+  double acc_ms[2][3] = {};
+  int64_t calls[2] = {};
+};
+
+namespace {
+
+int check_op(const fftmv_op* op) {
+  if (!op) return fail(FFTMV_EINVAL, "null operator");
+  std::lock_guard<std::mutex> g(g_reg_mu);
+  if (!g_live.count(op)) return fail(FFTMV_ESTATE, "operator handle is not live (freed or never created)");
+  return FFTMV_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int check_prec(const fftmv_precision* p) {
+  if (!p) return fail(FFTMV_EINVAL, "null precision");
+  const int32_t v[5] = {p->pad, p->fft, p->gemv, p->ifft, p->unpad};
+  for (int i = 0; i < 5; ++i)
+    if (v[i] != FFTMV_F64 && v[i] != FFTMV_F32) return fail(FFTMV_EINVAL, "phase %d precision %d is not F64/F32", i, v[i]);
+  if (p->gemv_mode != FFTMV_GEMV_NATIVE && p->gemv_mode != FFTMV_GEMV_F64X2F32)
+    return fail(FFTMV_EINVAL, "gemv_mode %d unknown", p->gemv_mode);
+  if (p->gemv_mode == FFTMV_GEMV_F64X2F32 && p->gemv != FFTMV_F64)
+    return fail(FFTMV_EINVAL, "gemv_mode F64X2F32 needs an FP64 GEMV phase");
+  return FFTMV_OK;
+}
+
+int gemv_kind(const fftmv_precision& p) {
+  if (p.gemv == FFTMV_F32) return GEMV_F32;
+  return p.gemv_mode == FFTMV_GEMV_F64X2F32 ? GEMV_DF : GEMV_F64;
+}
+
+const void* fhat_for(const fftmv_op* op, int kind) {
+  return kind == GEMV_F64 ? (const void*)op->fhat64 : kind == GEMV_DF ? (const void*)op->fhat_df : (const void*)op->fhat32;
+}
+
+void release(fftmv_op* op) {
+  cudaFree(op->tw64);
+  cudaFree(op->tw32);
+  cudaFree(op->fhat64);
+  cudaFree(op->fhat_df);
+  cudaFree(op->fhat32);
+  if (op->pool) cudaMemPoolDestroy(op->pool);
+  for (auto& s : op->free_sets)
+    for (auto e : s.ev) cudaEventDestroy(e);
+  for (auto& s : op->pending)
+    for (auto e : s.ev) cudaEventDestroy(e);
+  cudaGetLastError();
+}
+
+// Scratch layout of one call: the two spectra and optional host-I/O staging.
+struct CallPlan {
+  int kind, in_fmt, out_fmt;
+  int64_t Cin, Cout;       // input / output channels
+  int64_t in_ld, out_ld;   // spectral row length of the input / output side
+  size_t in_hat, out_hat;  // bytes
+};
+
+CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
+  CallPlan c{};
+  const fftmv_precision& p = op->prec[which];
+  c.kind = gemv_kind(p);
+  c.in_fmt = gemv_in_fmt(c.kind);
+  c.out_fmt = gemv_out_fmt(c.kind);
+  const bool fwd = which == FFTMV_FORWARD;
+  c.Cin = fwd ? op->Nm : op->Nd;
+  c.Cout = fwd ? op->Nd : op->Nm;
+  c.in_ld = fwd ? op->ldn : op->Nd;
+  c.out_ld = fwd ? op->Nd : op->ldn;
+  c.in_hat = align256((size_t)K * op->Nf * c.in_ld * fmt_bytes(c.in_fmt));
+  c.out_hat = align256((size_t)K * op->Nf * c.out_ld * fmt_bytes(c.out_fmt));
+  return c;
+}
+
+int run_matvec(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io, void* stream) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (K < 0) return fail(FFTMV_EINVAL, "K = %lld < 0", (long long)K);
+  if (io != FFTMV_IO_F64 && io != FFTMV_IO_F32) return fail(FFTMV_EINVAL, "io_dtype %d unknown", io);
+  if (K == 0) return FFTMV_OK;
+  if (!in || !out) return fail(FFTMV_EINVAL, "null input or output");
+  if (K > 65535) return fail(FFTMV_EUNSUPPORTED, "K = %lld exceeds 65535 right-hand sides per call", (long long)K);
+  DeviceGuard dg(op->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const CallPlan c = plan_call(op, which, K);
+  const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
+  const size_t in_bytes = (size_t)K * op->Nt * c.Cin * esz;
+  const size_t out_bytes = (size_t)K * op->Nt * c.Cout * esz;
+  {
+    const char* a = static_cast<const char*>(in);
+    const char* b = static_cast<const char*>(out);
+    if (a < b + out_bytes && b < a + in_bytes) return fail(FFTMV_EINVAL, "input and output overlap");
+  }
+  const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
+  const size_t stage_in = in_dev ? 0 : align256(in_bytes);
+  const size_t stage_out = out_dev ? 0 : align256(out_bytes);
+  const size_t total = c.in_hat + c.out_hat + stage_in + stage_out;
+
+  char* ws = nullptr;
+  CUDA_TRY(cudaMallocFromPoolAsync((void**)&ws, total, op->pool, s));
+  char* in_hat = ws;
+  char* out_hat = ws + c.in_hat;
+  const void* x = in;
+  void* y = out;
+  if (!in_dev) {
+    void* st = out_hat + c.out_hat;
+    cudaError_t e = cudaMemcpyAsync(st, in, in_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(ws, s);
+      return cuda_fail(e, "cudaMemcpyAsync(host input)");
+    }
+    x = st;
+  }
+  if (!out_dev) y = out_hat + c.out_hat + stage_in;
+
+  const fftmv_precision& p = op->prec[which];
+  const bool fft32 = p.fft == FFTMV_F32, ifft32 = p.ifft == FFTMV_F32;
+  const bool fwd = which == FFTMV_FORWARD;
+
+  TimingSet ts{};
+  bool timed = false;
+  if (op->timing) {
+    std::lock_guard<std::mutex> g(op->mu);
+    if (!op->free_sets.empty()) {
+      ts = op->free_sets.back();
+      op->free_sets.pop_back();
+      timed = true;
+    } else {
+      timed = true;
+      for (auto& e : ts.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) timed = false;
+      cudaGetLastError();
+    }
+    ts.which = which;
+  }
+
+  cudaError_t e = cudaSuccess;
+  if (timed) cudaEventRecord(ts.ev[0], s);
+  {  // phases 1-2
+    FwdDesc f{};
+    f.plan = op->plan;
+    f.tw = fft32 ? (const void*)op->tw32 : (const void*)op->tw64;
+    f.x = x;
+    f.X = in_hat;
+    f.Nt = (int)op->Nt;
+    f.rows = 1;
+    f.cols = (int)c.Cin;
+    f.out_cols = (int)c.in_ld;
+    f.K = (int)K;
+    f.x_ld_t = c.Cin;
+    f.x_ld_row = 0;
+    f.x_ld_b = op->Nt * c.Cin;
+    f.X_ld_w = c.in_ld;
+    f.X_ld_row = 0;
+    f.X_ld_b = op->Nf * c.in_ld;
+    f.fmt = c.in_fmt;
+    f.pad_single = p.pad == FFTMV_F32;
+    e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fft32, s);
+  }
+  if (timed) cudaEventRecord(ts.ev[1], s);
+  if (e == cudaSuccess) {  // phase 3
+    GemvDesc g{};
+    g.F = fhat_for(op, c.kind);
+    g.x = in_hat;
+    g.y = out_hat;
+    g.Nf = (int)op->Nf;
+    g.Nd = (int)op->Nd;
+    g.ldn = (int)op->ldn;
+    g.K = (int)K;
+    g.x_ld_b = op->Nf * c.in_ld;
+    g.y_ld_b = op->Nf * c.out_ld;
+    e = fwd ? launch_gemv_n(c.kind, g, s) : launch_gemv_h(c.kind, g, s);
+  }
+  if (timed) cudaEventRecord(ts.ev[2], s);
+  if (e == cudaSuccess) {  // phases 4-5
+    InvDesc v{};
+    v.plan = op->plan;
+    v.tw = ifft32 ? (const void*)op->tw32 : (const void*)op->tw64;
+    v.X = out_hat;
+    v.y = y;
+    v.Nt = (int)op->Nt;
+    v.cols = (int)c.Cout;
+    v.K = (int)K;
+    v.X_ld_w = c.out_ld;
+    v.X_ld_b = op->Nf * c.out_ld;
+    v.y_ld_t = c.Cout;
+    v.y_ld_b = op->Nt * c.Cout;
+    v.in_fmt = c.out_fmt;
+    v.unpad_single = p.unpad == FFTMV_F32;
+    e = launch_irfft_inv(v, ifft32, io == FFTMV_IO_F32, s);
+  }
+  if (timed) {
+    cudaEventRecord(ts.ev[3], s);
+    std::lock_guard<std::mutex> g(op->mu);
+    op->pending.push_back(ts);
+  }
+  if (e == cudaSuccess && !out_dev) e = cudaMemcpyAsync(out, y, out_bytes, cudaMemcpyDeviceToHost, s);
+  cudaError_t ef = cudaFreeAsync(ws, s);
+  if (e != cudaSuccess) return cuda_fail(e, "matvec kernels");
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  if (!in_dev || !out_dev) CUDA_TRY(cudaStreamSynchronize(s));
+  return FFTMV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fftmv_version(void) { return 100; }
+
+const char* fftmv_last_error(void) { return g_err.c_str(); }
+
+int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t Nm, void* stream, fftmv_op** out) {
+  if (!out) return fail(FFTMV_EINVAL, "null output handle");
+  *out = nullptr;
+  if (!F_col) return fail(FFTMV_EINVAL, "null block column");
+  if (Nt < 1 || Nd < 1 || Nm < 1) return fail(FFTMV_EINVAL, "sizes must be >= 1 (Nt=%lld Nd=%lld Nm=%lld)",
+                                              (long long)Nt, (long long)Nd, (long long)Nm);
+  const int64_t L = choose_length(Nt);
+  if (L > fft_max_length(false))
+    return fail(FFTMV_EUNSUPPORTED, "FFT length %lld for Nt=%lld exceeds the shared-memory FFT limit %d",
+                (long long)L, (long long)Nt, fft_max_length(false));
+  const int64_t ldn = (Nm + 7) / 8 * 8;
+  const int64_t Nf = L / 2 + 1;
+  if (Nd * ldn > INT32_MAX || ldn > INT32_MAX / 2 || Nf * Nd > INT32_MAX)
+    return fail(FFTMV_EUNSUPPORTED, "Nd * Nm too large");
+
+  fftmv_op* op = new (std::nothrow) fftmv_op();
+  if (!op) return fail(FFTMV_ENOMEM, "host allocation failed");
+  op->Nt = Nt;
+  op->Nd = Nd;
+  op->Nm = Nm;
+  op->L = L;
+  op->Nf = Nf;
+  op->ldn = ldn;
+  op->plan = make_plan(L);
+  for (auto& p : op->prec) p = fftmv_precision{FFTMV_F64, FFTMV_F64, FFTMV_F64, FFTMV_F64, FFTMV_F64, FFTMV_GEMV_NATIVE};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  auto bail = [&](int code) {
+    release(op);
+    delete op;
+    return code;
+  };
+  auto cu = [&](cudaError_t e, const char* what) { return e == cudaSuccess ? 0 : bail(cuda_fail(e, what)); };
+  int rc;
+  if ((rc = cu(cudaGetDevice(&op->device), "cudaGetDevice"))) return rc;
+
+  // twiddles exp(-2 pi i j / L), evaluated in long double and rounded once
+  std::vector<double2> tw((size_t)L);
+  std::vector<float2> tw32((size_t)L);
+  for (int64_t j = 0; j < L; ++j) {
+    const long double a = -2.0L * 3.141592653589793238462643383279502884L * (long double)j / (long double)L;
+    tw[j] = make_double2((double)cosl(a), (double)sinl(a));
+    tw32[j] = make_float2((float)cosl(a), (float)sinl(a));
+  }
+  if ((rc = cu(cudaMalloc(&op->tw64, L * sizeof(double2)), "cudaMalloc(twiddles)"))) return rc;
+  if ((rc = cu(cudaMalloc(&op->tw32, L * sizeof(float2)), "cudaMalloc(twiddles)"))) return rc;
+  if ((rc = cu(cudaMemcpy(op->tw64, tw.data(), L * sizeof(double2), cudaMemcpyHostToDevice), "twiddle copy"))) return rc;
+  if ((rc = cu(cudaMemcpy(op->tw32, tw32.data(), L * sizeof(float2), cudaMemcpyHostToDevice), "twiddle copy"))) return rc;
+
+  const size_t fh_elems = (size_t)Nf * Nd * ldn;
+  if ((rc = cu(cudaMalloc(&op->fhat64, fh_elems * sizeof(double2)), "cudaMalloc(F-hat)"))) return rc;
+
+  FwdDesc f{};
+  f.plan = op->plan;
+  f.tw = op->tw64;
+  f.Nt = (int)Nt;
+  f.cols = (int)Nm;
+  f.out_cols = (int)ldn;
+  f.K = 1;
+  f.x_ld_row = Nm;
+  f.x_ld_b = 0;
+  f.X_ld_w = Nd * ldn;
+  f.X_ld_row = ldn;
+  f.X_ld_b = 0;
+  f.fmt = FMT_C128;
+  f.pad_single = 0;
+  if (is_device_ptr(F_col)) {
+    f.x = F_col;
+    f.X = op->fhat64;
+    f.rows = (int)Nd;
+    f.x_ld_t = Nd * Nm;
+    if ((rc = cu(launch_rfft_fwd(f, false, false, s), "setup FFT"))) return rc;
+  } else {
+    // stage row blocks of the host block column through a bounded device buffer
+    const size_t row_bytes = (size_t)Nt * Nm * sizeof(double);
+    int64_t rc_rows = (int64_t)((size_t(1) << 30) / row_bytes);
+    if (rc_rows < 1) rc_rows = 1;
+    if (rc_rows > Nd) rc_rows = Nd;
+    double* stage = nullptr;
+    if ((rc = cu(cudaMalloc(&stage, rc_rows * row_bytes), "cudaMalloc(setup staging)"))) return rc;
+    for (int64_t r0 = 0; r0 < Nd; r0 += rc_rows) {
+      const int64_t nr = Nd - r0 < rc_rows ? Nd - r0 : rc_rows;
+      cudaError_t e = cudaMemcpy2DAsync(stage, nr * Nm * sizeof(double), F_col + r0 * Nm, Nd * Nm * sizeof(double),
+                                        nr * Nm * sizeof(double), Nt, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) {
+        f.x = stage;
+        f.X = op->fhat64 + r0 * ldn;
+        f.rows = (int)nr;
+        f.x_ld_t = nr * Nm;
+        e = launch_rfft_fwd(f, false, false, s);
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        cudaFree(stage);
+        return bail(cuda_fail(e, "setup FFT (host block column)"));
+      }
+    }
+    cudaFree(stage);
+  }
+  if ((rc = cu(cudaStreamSynchronize(s), "setup synchronize"))) return rc;
+
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = op->device;
+  if ((rc = cu(cudaMemPoolCreate(&op->pool, &props), "cudaMemPoolCreate"))) return rc;
+  uint64_t keep = UINT64_MAX;
+  if ((rc = cu(cudaMemPoolSetAttribute(op->pool, cudaMemPoolAttrReleaseThreshold, &keep), "pool attribute"))) return rc;
+
+  {
+    std::lock_guard<std::mutex> g(g_reg_mu);
+    g_live.insert(op);
+  }
+  *out = op;
+  return FFTMV_OK;
+}
+
+int fftmv_set_precision(fftmv_op* op, int which, const fftmv_precision* prec) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (which != FFTMV_FORWARD && which != FFTMV_ADJOINT) return fail(FFTMV_EINVAL, "which=%d is not F/F*", which);
+  if ((rc = check_prec(prec))) return rc;
+  DeviceGuard dg(op->device);
+  const int kind = gemv_kind(*prec);
+  const size_t n = (size_t)op->Nf * op->Nd * op->ldn;
+  if (kind == GEMV_DF && !op->fhat_df) {
+    CUDA_TRY(cudaMalloc(&op->fhat_df, n * sizeof(float4)));
+    CUDA_TRY(launch_convert_fhat(kind, op->fhat64, op->fhat_df, n, 0));
+    CUDA_TRY(cudaStreamSynchronize(0));
+  } else if (kind == GEMV_F32 && !op->fhat32) {
+    CUDA_TRY(cudaMalloc(&op->fhat32, n * sizeof(float2)));
+    CUDA_TRY(launch_convert_fhat(kind, op->fhat64, op->fhat32, n, 0));
+    CUDA_TRY(cudaStreamSynchronize(0));
+  }
+  op->prec[which] = *prec;
+  return FFTMV_OK;
+}
+
+int fftmv_get_precision(const fftmv_op* op, int which, fftmv_precision* out) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (which != FFTMV_FORWARD && which != FFTMV_ADJOINT) return fail(FFTMV_EINVAL, "which=%d is not F/F*", which);
+  if (!out) return fail(FFTMV_EINVAL, "null output");
+  *out = op->prec[which];
+  return FFTMV_OK;
+}
+
+int fftmv_matvec(fftmv_op* op, const void* m, void* d, int64_t K, int io_dtype, void* stream) {
+  return run_matvec(op, FFTMV_FORWARD, m, d, K, io_dtype, stream);
+}
+
+int fftmv_rmatvec(fftmv_op* op, const void* d, void* m, int64_t K, int io_dtype, void* stream) {
+  return run_matvec(op, FFTMV_ADJOINT, d, m, K, io_dtype, stream);
+}
+
+int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (which != FFTMV_FORWARD && which != FFTMV_ADJOINT) return fail(FFTMV_EINVAL, "which=%d is not F/F*", which);
+  if (K < 0 || !out) return fail(FFTMV_EINVAL, "bad K or null output");
+  const CallPlan c = plan_call(op, which, K);
+  *out = c.in_hat + c.out_hat;
+  return FFTMV_OK;
+}
+
+int fftmv_get_info(const fftmv_op* op, fftmv_info* out) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (!out) return fail(FFTMV_EINVAL, "null output");
+  out->Nt = op->Nt;
+  out->Nd = op->Nd;
+  out->Nm = op->Nm;
+  out->L = op->L;
+  out->Nf = op->Nf;
+  out->ldn = op->ldn;
+  out->device = op->device;
+  const size_t n = (size_t)op->Nf * op->Nd * op->ldn;
+  out->fhat_bytes = n * sizeof(double2) + (op->fhat_df ? n * sizeof(float4) : 0) + (op->fhat32 ? n * sizeof(float2) : 0);
+  return FFTMV_OK;
+}
+
+int fftmv_set_timing(fftmv_op* op, int enable) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  op->timing = enable != 0;
+  return FFTMV_OK;
+}
+
+int fftmv_phase_times(fftmv_op* op, int which, double ms_out[3], int64_t* calls_out) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (which != FFTMV_FORWARD && which != FFTMV_ADJOINT) return fail(FFTMV_EINVAL, "which=%d is not F/F*", which);
+  if (!ms_out) return fail(FFTMV_EINVAL, "null output");
+  DeviceGuard dg(op->device);
+  std::lock_guard<std::mutex> g(op->mu);
+  for (auto& ts : op->pending) {
+    CUDA_TRY(cudaEventSynchronize(ts.ev[3]));
+    for (int i = 0; i < 3; ++i) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, ts.ev[i], ts.ev[i + 1]));
+      op->acc_ms[ts.which][i] += ms;
+    }
+    op->calls[ts.which] += 1;
+    op->free_sets.push_back(ts);
+  }
+  op->pending.clear();
+  for (int i = 0; i < 3; ++i) ms_out[i] = op->acc_ms[which][i];
+  if (calls_out) *calls_out = op->calls[which];
+  return FFTMV_OK;
+}
+
+int fftmv_reset_timing(fftmv_op* op) {
+  double tmp[3];
+  int rc = fftmv_phase_times(op, FFTMV_FORWARD, tmp, nullptr);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> g(op->mu);
+  memset(op->acc_ms, 0, sizeof op->acc_ms);
+  op->calls[0] = op->calls[1] = 0;
+  return FFTMV_OK;
+}
+
+int fftmv_free(fftmv_op* op) {
+  if (!op) return FFTMV_OK;
+  {
+    std::lock_guard<std::mutex> g(g_reg_mu);
+    if (!g_live.erase(op)) return fail(FFTMV_ESTATE, "operator handle is not live (double free?)");
+  }
+  DeviceGuard dg(op->device);
+  cudaDeviceSynchronize();
+  release(op);
+  delete op;
+  return FFTMV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the C ABI (include/fftmv.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace fftmv {
+
+// Storage formats of complex arrays between phases.
+enum CFmt : int {
+  FMT_C128 = 0,  // double2 (re, im)
+  FMT_C64 = 1,   // float2 (re, im)
+  FMT_DF = 2,    // float4 (re_hi, im_hi, re_lo, im_lo): value = hi + lo, |lo| <= ulp(hi)/2
+};
+
+// Arithmetic used by the per-frequency block matvec (phase 3).
+enum GemvKind : int {
+  GEMV_F64 = 0,   // FP64 F-hat, FP64 FMA
+  GEMV_DF = 1,    // FP64-class: F-hat as FP32 hi/lo pairs, double-float arithmetic on the FP32 pipe
+  GEMV_F32 = 2,   // FP32 F-hat, FP32 FMA
+};
+
+constexpr int kMaxPasses = 16;
+
+// A mixed-radix (2, 3, 4, 5, 8) complex FFT of length L done in shared memory.
+struct FftPlan {
+  int L;
+  int npass;
+  int rad[kMaxPasses];
+};
+
+// Forward real FFT of zero-padded channels (phases 1-2 fused).
+// Channel c = (row, col) with col < cols; channels (2q, 2q+1) of a row are
+// transformed together as one complex signal.  x[b][t][row][col] is read for
+// t < Nt; X[b][w][row][col] is written for w < L/2+1 and col < out_cols
+// (columns cols..out_cols-1 are written as zeros).
+struct FwdDesc {
+  FftPlan plan;
+  const void* tw;          // twiddles exp(-2 pi i j / L), j < L (double2 or float2)
+  const void* x;           // real input (double or float)
+  void* X;                 // complex output in format fmt
+  int Nt;
+  int rows, cols, out_cols;
+  int K;                   // right-hand sides (grid.y)
+  int64_t x_ld_t, x_ld_row, x_ld_b;     // element strides of x
+  int64_t X_ld_w, X_ld_row, X_ld_b;     // complex-element strides of X
+  int fmt;                 // CFmt of X
+  int pad_single;          // round the loaded input to FP32 (pad phase in FP32)
+};
+
+// Inverse real FFT of Hermitian half spectra followed by unpad (phases 4-5 fused).
+// X[b][w][col] (w < L/2+1, format in_fmt) -> y[b][t][col] for t < Nt, scaled by 1/L.
+struct InvDesc {
+  FftPlan plan;
+  const void* tw;
+  const void* X;
+  void* y;
+  int Nt;
+  int cols;
+  int K;
+  int64_t X_ld_w, X_ld_b;  // complex-element strides
+  int64_t y_ld_t, y_ld_b;  // element strides
+  int in_fmt;              // FMT_C128 or FMT_C64
+  int unpad_single;        // round the result to FP32 before the output cast
+};
+
+// Per-frequency block matvec (phase 3) for K right-hand sides.
+// F-hat is [Nf][Nd][ldn] complex in the kind's storage; ldn is a multiple of 8.
+//  N (F):  y[b][w][r] = sum_n F[w][r][n] x[b][w][n]         x: [K][Nf][ldn], y: [K][Nf][Nd]
+//  H (F*): y[b][w][n] = sum_r conj(F[w][r][n]) x[b][w][r]   x: [K][Nf][Nd],  y: [K][Nf][ldn]
+struct GemvDesc {
+  const void* F;
+  const void* x;
+  void* y;
+  int Nf, Nd, ldn, K;
+  int64_t x_ld_b, y_ld_b;  // complex-element strides between right-hand sides
+};
+
+cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, bool fft_f32, cudaStream_t s);
+cudaError_t launch_irfft_inv(const InvDesc& d, bool fft_f32, bool out_f32, cudaStream_t s);
+cudaError_t launch_gemv_n(int kind, const GemvDesc& d, cudaStream_t s);
+cudaError_t launch_gemv_h(int kind, const GemvDesc& d, cudaStream_t s);
+// master FP64 F-hat (double2, n elements) -> kind's storage (DF float4 or F32 float2)
+cudaError_t launch_convert_fhat(int kind, const double2* master, void* out, size_t n, cudaStream_t s);
+
+size_t fft_smem_bytes(int L, bool fft_f32);
+int fft_max_length(bool fft_f32);
+// the input / output format each GEMV kind expects / produces
+int gemv_in_fmt(int kind);
+int gemv_out_fmt(int kind);
+size_t fmt_bytes(int fmt);
+
+}  // namespace fftmv

@@ -1,0 +1,207 @@
+"""Python face of the C ABI: the same entry points, argument marshalling only.
+
+Every step of a matvec runs in libfftmv.so's CUDA kernels.  Arrays may be
+torch tensors (CUDA or CPU) or numpy arrays (host).  Host arrays go through
+the library's host-I/O path (staged copies inside the call).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+_PHASE_LETTERS = {"d": L.FFTMV_F64, "s": L.FFTMV_F32}
+_MODES = {"native": L.FFTMV_GEMV_NATIVE, "f64x2f32": L.FFTMV_GEMV_F64X2F32}
+_WHICH = {"F": L.FFTMV_FORWARD, "forward": L.FFTMV_FORWARD, L.FFTMV_FORWARD: L.FFTMV_FORWARD,
+          "F*": L.FFTMV_ADJOINT, "adjoint": L.FFTMV_ADJOINT, L.FFTMV_ADJOINT: L.FFTMV_ADJOINT}
+
+
+def make_precision(prec: str = "ddddd", mode: str = "native") -> L.Precision:
+    """Precision struct from a 5-letter phase string over d/s (Section 3.2) and a GEMV mode."""
+    if len(prec) != 5 or any(c not in "ds" for c in prec):
+        raise ValueError(f"precision must be 5 letters over d/s, got {prec!r}")
+    if mode not in _MODES:
+        raise ValueError(f"mode must be one of {sorted(_MODES)}")
+    v = [_PHASE_LETTERS[c] for c in prec]
+    return L.Precision(*v, _MODES[mode])
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _array_info(x):
+    """(data pointer, io code, shape, is_cuda, device index)."""
+    if _is_torch(x):
+        torch = _torch()
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if x.dtype == torch.float64:
+            io = L.FFTMV_IO_F64
+        elif x.dtype == torch.float32:
+            io = L.FFTMV_IO_F32
+        else:
+            raise TypeError(f"dtype {x.dtype} not supported (float64 or float32)")
+        return x.data_ptr(), io, tuple(x.shape), x.is_cuda, (x.device.index if x.is_cuda else None)
+    x = np.asarray(x)
+    if not x.flags.c_contiguous:
+        raise ValueError("array must be C-contiguous")
+    if x.dtype == np.float64:
+        io = L.FFTMV_IO_F64
+    elif x.dtype == np.float32:
+        io = L.FFTMV_IO_F32
+    else:
+        raise TypeError(f"dtype {x.dtype} not supported (float64 or float32)")
+    return x.ctypes.data, io, x.shape, False, None
+
+
+def _stream_handle(stream, device) -> int:
+    if stream is None:
+        if device is None:
+            return 0
+        return _torch().cuda.current_stream(device).cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def create_operator(F_col, stream=None) -> "Operator":
+    """Operator from its first block column F_col[k, r, n] (FP64; host or device)."""
+    return Operator(F_col, stream=stream)
+
+
+class Operator:
+    """A block lower-triangular Toeplitz operator resident on one GPU."""
+
+    def __init__(self, F_col, stream=None):
+        ptr, io, shape, is_cuda, dev = _array_info(F_col)
+        if io != L.FFTMV_IO_F64 or len(shape) != 3:
+            raise ValueError("F_col must be a float64 array of shape (Nt, Nd, Nm)")
+        lib = L.lib()
+        if is_cuda:
+            _torch().cuda.set_device(dev)
+        h = ctypes.c_void_p()
+        L.check(lib.fftmv_create_operator(ptr, shape[0], shape[1], shape[2],
+                                          _stream_handle(stream, dev), ctypes.byref(h)))
+        self._h = h
+        info = L.Info()
+        L.check(lib.fftmv_get_info(self._h, ctypes.byref(info)))
+        self.Nt, self.Nd, self.Nm = info.Nt, info.Nd, info.Nm
+        self.L, self.Nf, self.ldn, self.device = info.L, info.Nf, info.ldn, info.device
+
+    # -- lifetime -----------------------------------------------------------
+    def free(self) -> None:
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            L.check(L.lib().fftmv_free(h))
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise L.FftmvError(-5, "operator already freed")
+        return self._h
+
+    def info(self) -> L.Info:
+        info = L.Info()
+        L.check(L.lib().fftmv_get_info(self.handle, ctypes.byref(info)))
+        return info
+
+    # -- precision ------------------------------------------------------------
+    def set_precision(self, which, prec: str = "ddddd", mode: str = "native") -> None:
+        p = make_precision(prec, mode)
+        L.check(L.lib().fftmv_set_precision(self.handle, _WHICH[which], ctypes.byref(p)))
+
+    def get_precision(self, which) -> tuple[str, str]:
+        p = L.Precision()
+        L.check(L.lib().fftmv_get_precision(self.handle, _WHICH[which], ctypes.byref(p)))
+        s = "".join("d" if v == L.FFTMV_F64 else "s" for v in (p.pad, p.fft, p.gemv, p.ifft, p.unpad))
+        mode = {v: k for k, v in _MODES.items()}[p.gemv_mode]
+        return s, mode
+
+    def workspace_bytes(self, which, K: int = 1) -> int:
+        out = ctypes.c_size_t()
+        L.check(L.lib().fftmv_workspace_bytes(self.handle, _WHICH[which], K, ctypes.byref(out)))
+        return out.value
+
+    # -- matvecs ------------------------------------------------------------
+    def _apply(self, which: int, x, out, stream):
+        n_in, n_out = (self.Nm, self.Nd) if which == L.FFTMV_FORWARD else (self.Nd, self.Nm)
+        ptr, io, shape, is_cuda, dev = _array_info(x)
+        if len(shape) == 2:
+            K, out_shape = 1, (self.Nt, n_out)
+        elif len(shape) == 3:
+            K, out_shape = shape[0], (shape[0], self.Nt, n_out)
+        else:
+            raise ValueError("input must be (Nt, N) or (K, Nt, N)")
+        if tuple(shape[-2:]) != (self.Nt, n_in):
+            raise ValueError(f"input shape {shape} does not match (Nt={self.Nt}, N={n_in})")
+        if out is None:
+            if _is_torch(x):
+                out = _torch().empty(out_shape, dtype=x.dtype, device=x.device)
+            else:
+                out = np.empty(out_shape, dtype=np.asarray(x).dtype)
+        optr, oio, oshape, o_cuda, odev = _array_info(out)
+        if tuple(oshape) != tuple(out_shape) or oio != io:
+            raise ValueError(f"out must have shape {out_shape} and the input's dtype")
+        dev = dev if dev is not None else odev
+        fn = L.lib().fftmv_matvec if which == L.FFTMV_FORWARD else L.lib().fftmv_rmatvec
+        L.check(fn(self.handle, ptr, optr, K, io, _stream_handle(stream, dev)))
+        return out
+
+    def matvec(self, m, out=None, stream=None):
+        """d = F m (Section 2.4): m is (Nt, Nm) or (K, Nt, Nm); returns (.., Nt, Nd)."""
+        return self._apply(L.FFTMV_FORWARD, m, out, stream)
+
+    def rmatvec(self, d, out=None, stream=None):
+        """m = F* d (Section 2.4): d is (Nt, Nd) or (K, Nt, Nd); returns (.., Nt, Nm)."""
+        return self._apply(L.FFTMV_ADJOINT, d, out, stream)
+
+    # -- per-phase timers -----------------------------------------------------
+    def set_timing(self, enable: bool = True) -> None:
+        L.check(L.lib().fftmv_set_timing(self.handle, int(bool(enable))))
+
+    def phase_times(self, which) -> tuple[list[float], int]:
+        """Summed ms of [pad+FFT, block matvec, IFFT+unpad] and the call count."""
+        ms = (ctypes.c_double * 3)()
+        calls = ctypes.c_int64()
+        L.check(L.lib().fftmv_phase_times(self.handle, _WHICH[which], ms, ctypes.byref(calls)))
+        return list(ms), calls.value
+
+    def reset_timing(self) -> None:
+        L.check(L.lib().fftmv_reset_timing(self.handle))
+
+
+# the C ABI's verbs, for callers that prefer functions
+def set_precision(op: Operator, which, prec: str = "ddddd", mode: str = "native") -> None:
+    op.set_precision(which, prec, mode)
+
+
+def matvec(op: Operator, m, out=None, stream=None):
+    return op.matvec(m, out=out, stream=stream)
+
+
+def rmatvec(op: Operator, d, out=None, stream=None):
+    return op.rmatvec(d, out=out, stream=stream)
+
+
+def free(op: Operator) -> None:
+    op.free()

@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU FP64 oracle.
+
+Tolerances (relative L2 over the whole output, as the precision study of
+Section 4.2.1 measures it): <= 1e-12 for every FP64 configuration (native FP64
+and the FP64-class hi/lo GEMV); <= 1e-5 for any configuration with an FP32
+phase, whose error is also reported.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_2508_10202_gb300 import build
+    build.build()
+    return torch
+
+
+def make_case(Nt, Nd, Nm, K=1, seed=0, decay=None):
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=seed, decay=decay)
+    m = synth.vectors(synth.TAG_M, Nt, Nm, k=K, seed=seed)
+    d = synth.vectors(synth.TAG_D, Nt, Nd, k=K, seed=seed)
+    return Fcol, m, d
+
+
+def gpu_op(torch, Fcol):
+    from paper_2508_10202_gb300 import Operator
+    return Operator(torch.from_numpy(Fcol).cuda())
+
+
+def run_both(torch, op, m, d):
+    y = op.matvec(torch.from_numpy(m).cuda()).cpu().numpy()
+    x = op.rmatvec(torch.from_numpy(d).cuda()).cpu().numpy()
+    return y, x
+
+
+MODES64 = [("ddddd", "native"), ("ddddd", "f64x2f32")]
+
+
+# --- the plain FP64 workload: Nt=64, Nd=8, Nm=32, seed 0 ---------------------
+
+@pytest.mark.parametrize("prec,mode", MODES64)
+def test_small_fp64_workload(torch_cuda, prec, mode):
+    torch = torch_cuda
+    Fcol, m, d = make_case(64, 8, 32, seed=0)
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", prec, mode)
+    op.set_precision("F*", prec, mode)
+    y, x = run_both(torch, op, m[0], d[0])
+    assert oracle.rel_l2(y, oracle.matvec_direct(Fcol, m[0])) <= TOL64
+    assert oracle.rel_l2(x, oracle.rmatvec_direct(Fcol, d[0])) <= TOL64
+    op.free()
+
+
+# --- ragged and degenerate sizes: every radix, odd channel counts, tails -----
+
+SIZES = [(1, 1, 1), (2, 1, 3), (3, 2, 5), (5, 3, 7), (7, 9, 2), (8, 1, 33), (12, 5, 17), (25, 3, 40),
+         (64, 8, 32), (100, 13, 257), (125, 7, 100), (243, 4, 9), (300, 17, 513)]
+
+
+@pytest.mark.parametrize("Nt,Nd,Nm", SIZES)
+@pytest.mark.parametrize("prec,mode", MODES64 + [("dssdd", "native"), ("sssss", "native")])
+def test_sizes(torch_cuda, Nt, Nd, Nm, prec, mode):
+    torch = torch_cuda
+    Fcol, m, d = make_case(Nt, Nd, Nm, K=2, seed=Nt + 7 * Nd + 13 * Nm)
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", prec, mode)
+    op.set_precision("F*", prec, mode)
+    y, x = run_both(torch, op, m, d)
+    tol = TOL64 if prec == "ddddd" else TOL32
+    assert oracle.rel_l2(y, oracle.matvec_direct(Fcol, m)) <= tol
+    assert oracle.rel_l2(x, oracle.rmatvec_direct(Fcol, d)) <= tol
+    op.free()
+
+
+# --- closed forms on the GPU -------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["native", "f64x2f32"])
+@pytest.mark.parametrize("s", [0, 1, 17])
+def test_time_shift_on_gpu(torch_cuda, mode, s):
+    torch = torch_cuda
+    Nt, N = 40, 6
+    Fcol = np.zeros((Nt, N, N))
+    Fcol[s] = np.eye(N)
+    m = np.random.default_rng(s).standard_normal((Nt, N))
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", "ddddd", mode)
+    op.set_precision("F*", "ddddd", mode)
+    y, x = run_both(torch, op, m, m)
+    want = np.zeros_like(m)
+    want[s:] = m[: Nt - s]
+    want_adj = np.zeros_like(m)
+    want_adj[: Nt - s] = m[s:]
+    np.testing.assert_allclose(y, want, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(x, want_adj, rtol=0, atol=1e-13)
+    op.free()
+
+
+@pytest.mark.parametrize("prec,mode", MODES64)
+def test_adjoint_identity_on_gpu(torch_cuda, prec, mode):
+    torch = torch_cuda
+    Fcol, m, d = make_case(96, 11, 130, seed=3)
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", prec, mode)
+    op.set_precision("F*", prec, mode)
+    y, x = run_both(torch, op, m[0], d[0])
+    lhs, rhs = np.vdot(y, d[0]), np.vdot(m[0], x)
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(y) * np.linalg.norm(d[0])
+    op.free()
+
+
+# --- all 32 per-phase configurations (Section 3.2) ---------------------------
+
+ALL32 = ["".join(p) for p in itertools.product("ds", repeat=5)]
+
+
+def test_all_32_phase_configs(torch_cuda, record_property):
+    torch = torch_cuda
+    Nt, Nd, Nm = 50, 6, 70
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=5, perturb=True)
+    m = synth.vectors(synth.TAG_M, Nt, Nm, seed=5, perturb=True)[0]
+    d = synth.vectors(synth.TAG_D, Nt, Nd, seed=5, perturb=True)[0]
+    ref, refa = oracle.matvec_direct(Fcol, m), oracle.rmatvec_direct(Fcol, d)
+    Fh = oracle.spectrum(Fcol)
+    op = gpu_op(torch, Fcol)
+    errs = {}
+    for prec in ALL32:
+        op.set_precision("F", prec)
+        op.set_precision("F*", prec)
+        y, x = run_both(torch, op, m, d)
+        e, ea = oracle.rel_l2(y, ref), oracle.rel_l2(x, refa)
+        em = oracle.rel_l2(oracle.matvec_mixed(Fh, m, Nt, prec), ref)
+        errs[prec] = (e, ea, em)
+        tol = TOL64 if prec == "ddddd" else TOL32
+        assert e <= tol and ea <= tol, (prec, e, ea)
+        # the same order of magnitude as the emulated FP32 rounding
+        if prec[1:4] != "ddd":
+            assert e <= 30 * em + 1e-12, (prec, e, em)
+    record_property("errors", {k: [f"{v:.2e}" for v in t] for k, t in errs.items()})
+    op.free()
+
+
+# --- I/O forms -----------------------------------------------------------------
+
+def test_fp32_io_and_host_io(torch_cuda):
+    torch = torch_cuda
+    Fcol, m, d = make_case(30, 4, 21, K=3, seed=9)
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", "ddddd", "f64x2f32")
+    y_dev = op.matvec(torch.from_numpy(m).cuda()).cpu().numpy()
+    y_host = op.matvec(m)                                  # numpy in, numpy out
+    np.testing.assert_array_equal(y_dev, y_host)
+    y_pin = op.matvec(torch.from_numpy(m).pin_memory())    # pinned torch CPU tensor
+    np.testing.assert_array_equal(y_dev, y_pin.numpy())
+    m32 = m.astype(np.float32)
+    y32 = op.matvec(torch.from_numpy(m32).cuda()).cpu().numpy()
+    assert y32.dtype == np.float32
+    assert oracle.rel_l2(y32, oracle.matvec_direct(Fcol, m32.astype(np.float64))) <= TOL32
+    op.free()
+
+
+def test_host_block_column_equals_device_block_column(torch_cuda):
+    torch = torch_cuda
+    from paper_2508_10202_gb300 import Operator
+    Fcol, m, d = make_case(20, 5, 9, seed=4)
+    a = Operator(Fcol)
+    b = Operator(torch.from_numpy(Fcol).cuda())
+    ya, xa = run_both(torch, a, m[0], d[0])
+    yb, xb = run_both(torch, b, m[0], d[0])
+    np.testing.assert_array_equal(ya, yb)
+    np.testing.assert_array_equal(xa, xb)
+    a.free()
+    b.free()
+
+
+def test_deterministic_and_stream_concurrent(torch_cuda):
+    torch = torch_cuda
+    Fcol, m, d = make_case(64, 10, 300, K=2, seed=12)
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", "ddddd", "f64x2f32")
+    mt = torch.from_numpy(m).cuda()
+    ref = op.matvec(mt)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    outs = []
+    for s in streams:
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            outs.append(op.matvec(mt, stream=s))
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o, ref)
+    op.free()
+
+
+def test_empty_batch_and_errors(torch_cuda):
+    torch = torch_cuda
+    from paper_2508_10202_gb300 import FftmvError
+    Fcol, m, d = make_case(8, 2, 3, seed=1)
+    op = gpu_op(torch, Fcol)
+    out = op.matvec(torch.zeros((0, 8, 3), dtype=torch.float64, device="cuda"))
+    assert out.shape == (0, 8, 2)
+    with pytest.raises(ValueError):
+        op.matvec(torch.zeros((8, 4), dtype=torch.float64, device="cuda"))
+    with pytest.raises(FftmvError):
+        op.set_precision("F", "dsddd", "f64x2f32")  # hi/lo mode needs an FP64 GEMV phase
+    op.free()
+    with pytest.raises(FftmvError):
+        op.matvec(torch.from_numpy(m[0]).cuda())
+
+
+def test_timing_counters(torch_cuda):
+    torch = torch_cuda
+    Fcol, m, d = make_case(16, 3, 40, seed=2)
+    op = gpu_op(torch, Fcol)
+    op.set_timing(True)
+    mt = torch.from_numpy(m[0]).cuda()
+    for _ in range(3):
+        op.matvec(mt)
+    ms, calls = op.phase_times("F")
+    assert calls == 3 and all(v > 0 for v in ms)
+    op.reset_timing()
+    assert op.phase_times("F")[1] == 0
+    op.free()
