@@ -215,7 +215,7 @@ def test_empty_batch_and_errors(torch_cuda):
     with pytest.raises(ValueError):
         op.matvec(torch.zeros((8, 4), dtype=torch.float64, device="cuda"))
     with pytest.raises(FftmvError):
-        op.set_precision("F", "dsddd", "f64x2f32")  # hi/lo mode needs an FP64 GEMV phase
+        op.set_precision("F", "ddsdd", "f64x2f32")  # hi/lo mode needs an FP64 GEMV phase
     op.free()
     with pytest.raises(FftmvError):
         op.matvec(torch.from_numpy(m[0]).cuda())
