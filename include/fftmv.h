@@ -143,6 +143,36 @@ int fftmv_set_timing(fftmv_op* op, int enable);
 int fftmv_phase_times(fftmv_op* op, int which, double ms_out[3], int64_t* calls_out);
 int fftmv_reset_timing(fftmv_op* op);
 
+/* Size of the fixed device array behind fftmv_apply_noalloc: 64 MiB. */
+#define FFTMV_NOALLOC_SCRATCH_BYTES ((size_t)64 * 1024 * 1024)
+
+/* fftmv_apply_noalloc: F m (which = FFTMV_FORWARD) or F* d (which =
+ * FFTMV_ADJOINT) like fftmv_matvec / fftmv_rmatvec, but without allocating
+ * any memory.  The paper has no counterpart; this entry point exists for
+ * callers that cannot allocate device memory once they are running.  Examples
+ * are a process whose memory manager reserved the GPU's memory at start-up and
+ * allows no further cudaMalloc, and a latency-critical loop that must not risk
+ * an allocation failing, or a pool growing, in the middle of its work.
+ *   in, out : device pointers only.  Host buffers would need staging memory,
+ *             so they are rejected with FFTMV_EINVAL.  Layouts and dtypes as
+ *             for fftmv_matvec / fftmv_rmatvec.
+ *   K       : right-hand sides; the two intermediate spectra of the call must
+ *             fit in FFTMV_NOALLOC_SCRATCH_BYTES (fftmv_workspace_bytes tells
+ *             how much a call needs).  Larger calls are rejected with
+ *             FFTMV_EUNSUPPORTED and a message giving both sizes.
+ * Scratch.  The spectra live in one file-scope device array inside the
+ * library.  Every GPU that loads the library holds that array until the
+ * process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls on a device share the array, and
+ * it keeps the previous call's contents: the kernels overwrite every scratch
+ * entry before they read it, so nothing is cleared in between.  Calls that
+ * overlap on the GPU (different streams, or different operators on the same
+ * device) race on the array; serialise them.
+ * Errors as for fftmv_matvec.  Stream ordered and asynchronous. */
+int fftmv_apply_noalloc(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io_dtype,
+                        void* stream);
+
 /* Release every device resource of the operator.  NULL is a no-op.  Waits
  * for the operator's pending work. */
 int fftmv_free(fftmv_op* op);

@@ -53,6 +53,7 @@ SIGNATURES = {
     "fftmv_set_timing": (_INT, [_P, _INT]),
     "fftmv_phase_times": (_INT, [_P, _INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "fftmv_reset_timing": (_INT, [_P]),
+    "fftmv_apply_noalloc": (_INT, [_P, _INT, _P, _P, _I64, _INT, _P]),
     "fftmv_free": (_INT, [_P]),
     "fftmv_last_error": (ctypes.c_char_p, []),
     "fftmv_version": (_INT, []),

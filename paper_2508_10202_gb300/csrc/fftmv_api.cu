@@ -564,3 +564,122 @@ int fftmv_free(fftmv_op* op) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the matvec (include/fftmv.h: fftmv_apply_noalloc).
+// The paper has no counterpart.  The two intermediate spectra live in this
+// file-scope device array instead of the operator's pool.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char fftmv_noalloc_scratch[FFTMV_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+char* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current).
+// In host code the array's name is only a host-side stand-in, so the address
+// is looked up once per device and cached.
+int noalloc_address(int device, char** out) {
+  if (device < 0 || device >= kNoallocMaxDevices)
+    return fail(FFTMV_EUNSUPPORTED, "device %d beyond the %d devices the no-alloc path tracks", device,
+                kNoallocMaxDevices);
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, fftmv_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(fftmv_noalloc_scratch)");
+    g_noalloc_addr[device] = static_cast<char*>(p);
+  }
+  *out = g_noalloc_addr[device];
+  return FFTMV_OK;
+}
+
+}  // namespace
+
+extern "C" int fftmv_apply_noalloc(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io,
+                                   void* stream) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (which != FFTMV_FORWARD && which != FFTMV_ADJOINT) return fail(FFTMV_EINVAL, "which=%d is not F/F*", which);
+  if (K < 0) return fail(FFTMV_EINVAL, "K = %lld < 0", (long long)K);
+  if (io != FFTMV_IO_F64 && io != FFTMV_IO_F32) return fail(FFTMV_EINVAL, "io_dtype %d unknown", io);
+  if (K == 0) return FFTMV_OK;
+  if (!in || !out) return fail(FFTMV_EINVAL, "null input or output");
+  if (K > 65535) return fail(FFTMV_EUNSUPPORTED, "K = %lld exceeds 65535 right-hand sides per call", (long long)K);
+  DeviceGuard dg(op->device);
+  const CallPlan c = plan_call(op, which, K);
+  const size_t need = c.in_hat + c.out_hat;
+  if (need > FFTMV_NOALLOC_SCRATCH_BYTES)
+    return fail(FFTMV_EUNSUPPORTED, "this call needs %zu bytes of scratch; the no-alloc array holds %zu", need,
+                (size_t)FFTMV_NOALLOC_SCRATCH_BYTES);
+  const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
+  const size_t in_bytes = (size_t)K * op->Nt * c.Cin * esz;
+  const size_t out_bytes = (size_t)K * op->Nt * c.Cout * esz;
+  {
+    const char* a = static_cast<const char*>(in);
+    const char* b = static_cast<const char*>(out);
+    if (a < b + out_bytes && b < a + in_bytes) return fail(FFTMV_EINVAL, "input and output overlap");
+  }
+  if (!is_device_ptr(in) || !is_device_ptr(out))
+    return fail(FFTMV_EINVAL, "fftmv_apply_noalloc takes device pointers only (host I/O would need staging memory)");
+  char* ws = nullptr;
+  if ((rc = noalloc_address(op->device, &ws))) return rc;
+  char* in_hat = ws;
+  char* out_hat = ws + c.in_hat;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const fftmv_precision& p = op->prec[which];
+  const bool fft32 = p.fft == FFTMV_F32, ifft32 = p.ifft == FFTMV_F32;
+
+  FwdDesc f{};
+  f.plan = op->plan;
+  f.tw = fft32 ? (const void*)op->tw32 : (const void*)op->tw64;
+  f.x = in;
+  f.X = in_hat;
+  f.Nt = (int)op->Nt;
+  f.rows = 1;
+  f.cols = (int)c.Cin;
+  f.out_cols = (int)c.in_ld;
+  f.K = (int)K;
+  f.x_ld_t = c.Cin;
+  f.x_ld_b = op->Nt * c.Cin;
+  f.X_ld_w = c.in_ld;
+  f.X_ld_b = op->Nf * c.in_ld;
+  f.fmt = c.in_fmt;
+  f.pad_single = p.pad == FFTMV_F32;
+  cudaError_t e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fft32, s);
+  if (e == cudaSuccess) {
+    GemvDesc g{};
+    g.F = fhat_for(op, c.kind);
+    g.x = in_hat;
+    g.y = out_hat;
+    g.Nf = (int)op->Nf;
+    g.Nd = (int)op->Nd;
+    g.ldn = (int)op->ldn;
+    g.K = (int)K;
+    g.x_ld_b = op->Nf * c.in_ld;
+    g.y_ld_b = op->Nf * c.out_ld;
+    e = which == FFTMV_FORWARD ? launch_gemv_n(c.kind, g, s) : launch_gemv_h(c.kind, g, s);
+  }
+  if (e == cudaSuccess) {
+    InvDesc v{};
+    v.plan = op->plan;
+    v.tw = ifft32 ? (const void*)op->tw32 : (const void*)op->tw64;
+    v.X = out_hat;
+    v.y = out;
+    v.Nt = (int)op->Nt;
+    v.cols = (int)c.Cout;
+    v.K = (int)K;
+    v.X_ld_w = c.out_ld;
+    v.X_ld_b = op->Nf * c.out_ld;
+    v.y_ld_t = c.Cout;
+    v.y_ld_b = op->Nt * c.Cout;
+    v.in_fmt = c.out_fmt;
+    v.unpad_single = p.unpad == FFTMV_F32;
+    e = launch_irfft_inv(v, ifft32, io == FFTMV_IO_F32, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "no-alloc matvec kernels");
+  return FFTMV_OK;
+}

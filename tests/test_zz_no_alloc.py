@@ -1,0 +1,86 @@
+"""The allocation-free entry point, fftmv_apply_noalloc, against fftmv_matvec/rmatvec.
+
+fftmv_apply_noalloc serves callers that cannot allocate device memory once
+they are running: for example a process whose memory manager reserved the
+GPU's memory at start-up, or a latency-critical loop that must not risk an
+allocation failing or a pool growing mid-run.  Its intermediate spectra live
+in a fixed 64 MiB device array inside the library instead of the operator's
+pool.  This test calls it through the C ABI twice in a row (the array keeps
+the previous call's contents) and compares each result with the pooled entry
+point's, within the FP64 tolerance of the other parity tests.  It lives in
+its own file, named to be collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_2508_10202_gb300 import build
+    build.build()
+    from paper_2508_10202_gb300 import Operator, _lib
+    return torch, Operator, _lib, _lib.lib()
+
+
+def _noalloc(lib, op, which, x, out, stream):
+    K = x.shape[0] if x.dim() == 3 else 1
+    io = 0 if x.dtype.is_floating_point and x.element_size() == 8 else 1
+    return lib.fftmv_apply_noalloc(op.handle, which, x.data_ptr(), out.data_ptr(), K, io, stream.cuda_stream)
+
+
+@pytest.mark.parametrize("mode", ["native", "f64x2f32"])
+def test_noalloc_matches_pooled_entry_points(env, mode):
+    torch, Operator, L, lib = env
+    Nt, Nd, Nm, K = 64, 8, 32, 3
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=0)
+    m = torch.from_numpy(synth.vectors(synth.TAG_M, Nt, Nm, k=K, seed=0)).cuda()
+    d = torch.from_numpy(synth.vectors(synth.TAG_D, Nt, Nd, k=K, seed=0)).cuda()
+    op = Operator(torch.from_numpy(Fcol).cuda())
+    op.set_precision("F", "ddddd", mode)
+    op.set_precision("F*", "ddddd", mode)
+    stream = torch.cuda.current_stream()
+    ref_d = op.matvec(m).cpu().numpy()
+    ref_m = op.rmatvec(d).cpu().numpy()
+    for call in range(2):
+        y = torch.full((K, Nt, Nd), float("nan"), dtype=torch.float64, device="cuda")
+        x = torch.full((K, Nt, Nm), float("nan"), dtype=torch.float64, device="cuda")
+        assert _noalloc(lib, op, L.FFTMV_FORWARD, m, y, stream) == 0, lib.fftmv_last_error()
+        assert _noalloc(lib, op, L.FFTMV_ADJOINT, d, x, stream) == 0, lib.fftmv_last_error()
+        torch.cuda.synchronize()
+        assert oracle.rel_l2(y.cpu().numpy(), ref_d) <= TOL64, call
+        assert oracle.rel_l2(x.cpu().numpy(), ref_m) <= TOL64, call
+    # and against the oracle itself
+    assert oracle.rel_l2(y.cpu().numpy(), oracle.matvec_direct(Fcol, m.cpu().numpy())) <= TOL64
+    op.free()
+
+
+def test_noalloc_rejects_oversize_and_host_buffers(env):
+    torch, Operator, L, lib = env
+    Nt, Nd, Nm = 300, 4, 4000          # F needs Nf*ldn*16 = 301*4000*16 B per RHS
+    op = Operator(torch.from_numpy(synth.block_column(Nt, Nd, Nm, seed=1)).cuda())
+    K = 64                              # ~1.2 GB of spectra: beyond the fixed array
+    need = op.workspace_bytes("F", K)
+    assert need > 64 * 1024 * 1024
+    m = torch.zeros((K, Nt, Nm), dtype=torch.float64, device="cuda")
+    y = torch.zeros((K, Nt, Nd), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    assert _noalloc(lib, op, L.FFTMV_FORWARD, m, y, stream) == -3
+    assert b"holds" in lib.fftmv_last_error()
+    mh = np.zeros((Nt, Nm))
+    yh = np.zeros((Nt, Nd))
+    rc = lib.fftmv_apply_noalloc(op.handle, L.FFTMV_FORWARD, mh.ctypes.data, yh.ctypes.data, 1, 0,
+                                 stream.cuda_stream)
+    assert rc == -1 and b"device pointers" in lib.fftmv_last_error()
+    op.free()
