@@ -1,0 +1,72 @@
+"""Full-size parity on the paper-shaped operator (Nt=1000, Nd=100, Nm=10000).
+
+Same operator, inputs and launch configuration as bench.py.  The oracle cannot
+form the whole 1000x100x10000 product in test time, so it checks
+  * sampled outputs, each computed one by one from the Section 2.3 definition
+    (relative L2 over the sample: an unbiased estimate of the full error), and
+  * the adjoint identity <F m, d> = <m, F* d>, which holds at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+NT, ND, NM = 1000, 100, 10000
+CASES = [  # (F precision, F* precision, mode, tolerance)
+    ("ddddd", "ddddd", "f64x2f32", 1e-12),
+    ("ddddd", "ddddd", "native", 1e-12),
+    ("dssdd", "ddssd", "native", 1e-5),
+]
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_2508_10202_gb300 import Operator, build
+    build.build()
+    Fcol = synth.block_column(NT, ND, NM, seed=0, decay=200.0)
+    m = synth.vectors(synth.TAG_M, NT, NM, seed=0)[0]
+    d = synth.vectors(synth.TAG_D, NT, ND, seed=0)[0]
+    op = Operator(Fcol)
+    yield torch, Fcol, m, d, op
+    op.free()
+
+
+def sample_idx(n, hi0, hi1, seed):
+    rng = np.random.default_rng(seed)
+    idx = [(int(rng.integers(hi0)), int(rng.integers(hi1))) for _ in range(n)]
+    idx += [(0, 0), (hi0 - 1, hi1 - 1), (hi0 - 1, 0), (0, hi1 - 1)]   # the corners
+    return idx
+
+
+@pytest.mark.parametrize("pf,pa,mode,tol", CASES)
+def test_fullsize_sampled_and_adjoint(full, pf, pa, mode, tol):
+    torch, Fcol, m, d, op = full
+    op.set_precision("F", pf, mode)
+    op.set_precision("F*", pa, mode)
+    y = op.matvec(torch.from_numpy(m).cuda()).cpu().numpy()
+    x = op.rmatvec(torch.from_numpy(d).cuda()).cpu().numpy()
+    idx = sample_idx(40, NT, ND, 1)
+    ref = oracle.matvec_entries(Fcol, m, idx)
+    got = np.array([y[i, r] for i, r in idx])
+    assert oracle.rel_l2(got, ref) <= tol
+    idx = sample_idx(40, NT, NM, 2)
+    ref = oracle.rmatvec_entries(Fcol, d, idx)
+    got = np.array([x[j, n] for j, n in idx])
+    assert oracle.rel_l2(got, ref) <= tol
+    lhs, rhs = np.vdot(y, d), np.vdot(m, x)
+    assert abs(lhs - rhs) <= max(tol, 1e-12) * np.linalg.norm(y) * np.linalg.norm(d)
+    assert np.all(np.isfinite(y)) and np.all(np.isfinite(x))
+
+
+def test_fullsize_host_io_matches_device_io(full):
+    torch, Fcol, m, d, op = full
+    op.set_precision("F", "ddddd", "f64x2f32")
+    y_dev = op.matvec(torch.from_numpy(m).cuda()).cpu().numpy()
+    y_host = op.matvec(torch.from_numpy(m).pin_memory()).numpy()
+    np.testing.assert_array_equal(y_dev, y_host)
