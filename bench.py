@@ -45,12 +45,14 @@ DECAY = 200.0
 METRIC = "F/F* matvec/s & HBM-roofline frac, Nt=1000 Nd=100 Nm=1e4; served p50/p99 ms"
 UNIT = "matvec/s"
 WORKLOAD = "paper-shaped single operator Nt=1000 Nd=100 Nm=10000, F and F* matvec, 1 RHS"
-HEADLINE = ("ddddd", "f64x2f32")
+HEADLINE = ("ddddd", "f64x2f32", "f64x2f32")
+# (phase string, block-matvec mode, FP64 FFT mode) for F and for F*
 VARIANTS = {
-    "fp64_native": (("ddddd", "native"), ("ddddd", "native")),
-    "fp64_class_hilo": (("ddddd", "f64x2f32"), ("ddddd", "f64x2f32")),
-    "paper_mp_optimum": (("dssdd", "native"), ("ddssd", "native")),
-    "all_fp32": (("sssss", "native"), ("sssss", "native")),
+    "fp64_native": (("ddddd", "native", "native"), ("ddddd", "native", "native")),
+    "fp64_class_hilo": (("ddddd", "f64x2f32", "f64x2f32"), ("ddddd", "f64x2f32", "f64x2f32")),
+    "fp64_class_gemv_native_fft": (("ddddd", "f64x2f32", "native"), ("ddddd", "f64x2f32", "native")),
+    "paper_mp_optimum": (("dssdd", "native", "f64x2f32"), ("ddssd", "native", "f64x2f32")),
+    "all_fp32": (("sssss", "native", "native"), ("sssss", "native", "native")),
 }
 KERNELS_PER_MATVEC = 3
 
@@ -105,7 +107,7 @@ def algorithmic_bytes(Nt: int, Nd: int, Nm: int, fhat_entry_bytes: int, io_bytes
     return Nf * Nd * Nm * fhat_entry_bytes + Nt * Nm * io_bytes + Nt * Nd * io_bytes
 
 
-def fhat_entry_bytes(prec: str, mode: str) -> int:
+def fhat_entry_bytes(prec: str, *modes: str) -> int:
     return 8 if prec[2] == "s" else 16
 
 
@@ -416,10 +418,10 @@ def main(args) -> None:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2 (FP64-class double-float; FP64 FFTs)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2 (FP64-class double-float on the FP32 pipe)",
             "data": "synthetic (seeded N(0,1) blocks x exp(-k/200), N(0,1) vectors)",
             "config": {"workload": WORKLOAD, "Nt": Nt, "Nd": Nd, "Nm": Nm, "rhs": 1,
-                       "precision": "ddddd / block matvec f64x2f32", "parallelism": f"replicas x{world}",
+                       "precision": "ddddd, block matvec and FFTs in f64x2f32", "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2: F-hat is 16 GB per matvec, read once"},
             "gpu_launches": KERNELS_PER_MATVEC * 2 * args.steps,
             "rel_err": {"F": err_f, "Fstar": err_a, "how": "24 sampled outputs vs the oracle's definition"},

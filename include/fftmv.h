@@ -81,6 +81,8 @@ typedef struct {
   int32_t ifft;      /* phase 4, inverse FFT                                    */
   int32_t unpad;     /* phase 5, unpadding (output cast)                        */
   int32_t gemv_mode; /* fftmv_gemv_mode                                         */
+  int32_t fft_mode;  /* fftmv_gemv_mode values, for the FP64 FFT and IFFT phases:
+                        NATIVE = FP64 FMA; F64X2F32 = double-float on the FP32 pipe */
 } fftmv_precision;
 
 typedef enum { FFTMV_FORWARD = 0 /* F */, FFTMV_ADJOINT = 1 /* F* */ } fftmv_which;
@@ -105,15 +107,16 @@ typedef struct {
  *   stream : cudaStream_t used for the setup work (NULL = legacy default).
  *   out    : receives the new handle.
  * Creates on the current CUDA device.  Synchronous: returns after F-hat is
- * built.  Both F and F* start in all-FP64 precision, gemv_mode NATIVE. */
+ * built.  Both F and F* start in all-FP64 precision, gemv_mode and fft_mode
+ * NATIVE. */
 int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t Nm, void* stream,
                           fftmv_op** out);
 
 /* Set the per-phase precisions used by later calls for F (which=FORWARD) or
  * F* (which=ADJOINT) (Section 3.2: set at creation, changeable at runtime).
  * Builds the stored F-hat form the GEMV phase needs if it does not exist yet
- * (synchronously).  EINVAL for out-of-range values or F64X2F32 with an FP32
- * GEMV phase. */
+ * (synchronously).  EINVAL for out-of-range values or gemv_mode F64X2F32 with
+ * an FP32 GEMV phase.  fft_mode only affects phases set to FP64. */
 int fftmv_set_precision(fftmv_op* op, int which, const fftmv_precision* prec);
 int fftmv_get_precision(const fftmv_op* op, int which, fftmv_precision* out);
 

@@ -28,7 +28,8 @@ class FftmvError(RuntimeError):
 
 class Precision(ctypes.Structure):
     _fields_ = [("pad", ctypes.c_int32), ("fft", ctypes.c_int32), ("gemv", ctypes.c_int32),
-                ("ifft", ctypes.c_int32), ("unpad", ctypes.c_int32), ("gemv_mode", ctypes.c_int32)]
+                ("ifft", ctypes.c_int32), ("unpad", ctypes.c_int32), ("gemv_mode", ctypes.c_int32),
+                ("fft_mode", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -13,106 +13,254 @@
 // are zero in shared memory and never read from HBM, and only t < Nt is
 // written back.  Casts between the I/O dtype, the pad/unpad precision and the
 // FFT precision are fused into the loads and stores (Section 3.2).
+//
+// Arithmetic.  The same transform is instantiated for three precisions:
+//   double : FP64 FMA (GB300 runs it at ~1.2 TFLOP/s, so FP64 FFTs are
+//            FP64-pipe bound);
+//   float  : FP32;
+//   DFP    : double-float, an FP64-class format on the FP32 pipe.  A real is
+//            an unevaluated pair hi + lo of floats (|lo| <= ulp(hi)/2, about
+//            48 significant bits); sums use TwoSum + Fast2Sum renormalisation,
+//            products an FMA-exact TwoProd plus the hi*lo cross terms.  The
+//            adds are the normwise-accurate ("sloppy") double-word sums, which
+//            is the accuracy an FFT's normwise error analysis needs.
+
+#include <type_traits>
 
 #include "fftmv_internal.h"
 
 namespace fftmv {
 namespace {
 
-template <typename T> struct CxT;
-template <> struct CxT<double> { using type = double2; };
-template <> struct CxT<float> { using type = float2; };
+struct DFP {};  // precision tag: double-float on the FP32 pipe
 
-template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
-template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
-template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
-  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
-// multiply by -i (forward) or +i (inverse)
-template <bool INV, typename C> __device__ __forceinline__ C mul_mi(C a) {
-  return INV ? C{-a.y, a.x} : C{a.y, -a.x};
-}
-template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return {a.x * s, a.y * s}; }
+// a real constant in every precision: FP64 value and its FP32 hi/lo split
+struct Kc {
+  double d;
+  float h, l;
+};
+// cos/sin of 2 pi / 5, 4 pi / 5, pi / 3 and 1 / sqrt(2)
+__device__ constexpr Kc KC1{0.30901699437494742410, 0.30901700258255005f, -8.207602597565256e-09f};
+__device__ constexpr Kc KC2{-0.80901699437494742410, -0.80901700258255f, 8.207602597565256e-09f};
+__device__ constexpr Kc KS1{0.95105651629515357212, 0.9510565400123596f, -2.3717205976936384e-08f};
+__device__ constexpr Kc KS2{0.58778525229247312917, 0.5877852439880371f, 8.304436249773062e-09f};
+__device__ constexpr Kc KS3{0.86602540378443864676, 0.8660253882408142f, 1.5543625053737742e-08f};
+__device__ constexpr Kc KR2{0.70710678118654752440, 0.7071067690849304f, 1.2101617485882343e-08f};
 
-// Constants of the small DFTs (cos/sin of 2 pi / 5, 4 pi / 5, pi / 3, pi / 4).
-#define K_C1 0.30901699437494742410
-#define K_C2 (-0.80901699437494742410)
-#define K_S1 0.95105651629515357212
-#define K_S2 0.58778525229247312917
-#define K_S3 0.86602540378443864676
-#define K_R2 0.70710678118654752440
+// ---------------------------------------------------------------------------
+// double-float reals
+// ---------------------------------------------------------------------------
+struct dfr {
+  float h, l;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ dfr fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dfr{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfr df_add(dfr a, dfr b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  return fast_two_sum(s, e);
+}
+__device__ __forceinline__ dfr df_neg(dfr a) { return dfr{-a.h, -a.l}; }
+__device__ __forceinline__ dfr df_mul(dfr a, dfr b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+// a.re*b.re - s*a.im*b.im (s = +1) in one renormalisation
+__device__ __forceinline__ dfr df_dot2(dfr a, dfr b, dfr c, dfr d, float sgn) {
+  // a*b + sgn*c*d
+  const float p1 = __fmul_rn(a.h, b.h);
+  const float p2 = __fmul_rn(sgn * c.h, d.h);
+  float e1 = __fmaf_rn(a.h, b.h, -p1);
+  float e2 = __fmaf_rn(sgn * c.h, d.h, -p2);
+  float s, t;
+  two_sum(p1, p2, s, t);
+  t = __fadd_rn(t, __fadd_rn(e1, e2));
+  t = __fmaf_rn(a.h, b.l, t);
+  t = __fmaf_rn(a.l, b.h, t);
+  t = __fmaf_rn(sgn * c.h, d.l, t);
+  t = __fmaf_rn(sgn * c.l, d.h, t);
+  return fast_two_sum(s, t);
+}
+
+// ---------------------------------------------------------------------------
+// arithmetic traits: reals R, complexes C (the shared-memory element)
+// ---------------------------------------------------------------------------
+template <typename P> struct Ar;
+
+template <> struct Ar<double> {
+  using R = double;
+  using C = double2;
+  __device__ __forceinline__ static R add(R a, R b) { return a + b; }
+  __device__ __forceinline__ static R sub(R a, R b) { return a - b; }
+  __device__ __forceinline__ static R neg(R a) { return -a; }
+  __device__ __forceinline__ static R half(R a) { return 0.5 * a; }
+  __device__ __forceinline__ static R mulk(R a, const Kc& k) { return a * k.d; }
+  __device__ __forceinline__ static R re(C c) { return c.x; }
+  __device__ __forceinline__ static R im(C c) { return c.y; }
+  __device__ __forceinline__ static C mk(R r, R i) { return make_double2(r, i); }
+  __device__ __forceinline__ static C cmul(C a, C w) {
+    return make_double2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+  }
+  __device__ __forceinline__ static C conj(C a) { return make_double2(a.x, -a.y); }
+  __device__ __forceinline__ static R from_d(double x) { return x; }
+  __device__ __forceinline__ static R from_f(float x) { return x; }
+  __device__ __forceinline__ static double to_d(R x) { return x; }
+  __device__ __forceinline__ static float to_f(R x) { return (float)x; }
+  __device__ __forceinline__ static R zero() { return 0.0; }
+};
+
+template <> struct Ar<float> {
+  using R = float;
+  using C = float2;
+  __device__ __forceinline__ static R add(R a, R b) { return a + b; }
+  __device__ __forceinline__ static R sub(R a, R b) { return a - b; }
+  __device__ __forceinline__ static R neg(R a) { return -a; }
+  __device__ __forceinline__ static R half(R a) { return 0.5f * a; }
+  __device__ __forceinline__ static R mulk(R a, const Kc& k) { return a * (float)k.d; }
+  __device__ __forceinline__ static R re(C c) { return c.x; }
+  __device__ __forceinline__ static R im(C c) { return c.y; }
+  __device__ __forceinline__ static C mk(R r, R i) { return make_float2(r, i); }
+  __device__ __forceinline__ static C cmul(C a, C w) {
+    return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+  }
+  __device__ __forceinline__ static C conj(C a) { return make_float2(a.x, -a.y); }
+  __device__ __forceinline__ static R from_d(double x) { return (float)x; }
+  __device__ __forceinline__ static R from_f(float x) { return x; }
+  __device__ __forceinline__ static double to_d(R x) { return x; }
+  __device__ __forceinline__ static float to_f(R x) { return x; }
+  __device__ __forceinline__ static R zero() { return 0.f; }
+};
+
+// complex double-float stored as float4 (re_hi, im_hi, re_lo, im_lo): the
+// FMT_DF layout, so spectra move between phases without conversion
+template <> struct Ar<DFP> {
+  using R = dfr;
+  using C = float4;
+  __device__ __forceinline__ static R add(R a, R b) { return df_add(a, b); }
+  __device__ __forceinline__ static R sub(R a, R b) { return df_add(a, df_neg(b)); }
+  __device__ __forceinline__ static R neg(R a) { return df_neg(a); }
+  __device__ __forceinline__ static R half(R a) { return dfr{0.5f * a.h, 0.5f * a.l}; }
+  __device__ __forceinline__ static R mulk(R a, const Kc& k) { return df_mul(a, dfr{k.h, k.l}); }
+  __device__ __forceinline__ static R re(C c) { return dfr{c.x, c.z}; }
+  __device__ __forceinline__ static R im(C c) { return dfr{c.y, c.w}; }
+  __device__ __forceinline__ static C mk(R r, R i) { return make_float4(r.h, i.h, r.l, i.l); }
+  __device__ __forceinline__ static C cmul(C a, C w) {
+    const dfr ar = re(a), ai = im(a), wr = re(w), wi = im(w);
+    return mk(df_dot2(ar, wr, ai, wi, -1.f), df_dot2(ar, wi, ai, wr, 1.f));
+  }
+  __device__ __forceinline__ static C conj(C a) { return make_float4(a.x, -a.y, a.z, -a.w); }
+  __device__ __forceinline__ static R from_d(double x) {
+    const float h = (float)x;
+    return dfr{h, (float)(x - (double)h)};
+  }
+  __device__ __forceinline__ static R from_f(float x) { return dfr{x, 0.f}; }
+  __device__ __forceinline__ static double to_d(R x) { return (double)x.h + (double)x.l; }
+  __device__ __forceinline__ static float to_f(R x) { return __fadd_rn(x.h, x.l); }
+  __device__ __forceinline__ static R zero() { return dfr{0.f, 0.f}; }
+};
+
+// complex helpers built on the traits
+template <typename P> struct Cx {
+  using A = Ar<P>;
+  using C = typename A::C;
+  __device__ __forceinline__ static C add(C a, C b) { return A::mk(A::add(A::re(a), A::re(b)), A::add(A::im(a), A::im(b))); }
+  __device__ __forceinline__ static C sub(C a, C b) { return A::mk(A::sub(A::re(a), A::re(b)), A::sub(A::im(a), A::im(b))); }
+  __device__ __forceinline__ static C mulk(C a, const Kc& k) { return A::mk(A::mulk(A::re(a), k), A::mulk(A::im(a), k)); }
+  // multiply by -i (forward) or +i (inverse)
+  template <bool INV> __device__ __forceinline__ static C mmi(C a) {
+    return INV ? A::mk(A::neg(A::im(a)), A::re(a)) : A::mk(A::im(a), A::neg(A::re(a)));
+  }
+};
 
 // In-register DFT of size R: X_p = sum_q v_q exp(-+2 pi i q p / R).
-template <typename T, int R, bool INV> struct Dft;
+template <typename P, int R, bool INV> struct Dft;
 
-template <typename T, bool INV> struct Dft<T, 2, INV> {
-  using C = typename CxT<T>::type;
+template <typename P, bool INV> struct Dft<P, 2, INV> {
+  using C = typename Ar<P>::C;
   __device__ __forceinline__ static void run(C* v) {
-    C a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+    const C a = v[0], b = v[1];
+    v[0] = Cx<P>::add(a, b);
+    v[1] = Cx<P>::sub(a, b);
   }
 };
 
-template <typename T, bool INV> struct Dft<T, 3, INV> {
-  using C = typename CxT<T>::type;
+template <typename P, bool INV> struct Dft<P, 3, INV> {
+  using A = Ar<P>;
+  using C = typename A::C;
   __device__ __forceinline__ static void run(C* v) {
-    C s = cadd(v[1], v[2]);
-    C d = mul_mi<INV>(csub(v[1], v[2]));
-    C m = {v[0].x - T(0.5) * s.x, v[0].y - T(0.5) * s.y};
-    C dd = cscale(d, T(K_S3));
-    v[0] = cadd(v[0], s);
-    v[1] = cadd(m, dd);
-    v[2] = csub(m, dd);
+    const C s = Cx<P>::add(v[1], v[2]);
+    const C d = Cx<P>::mulk(Cx<P>::template mmi<INV>(Cx<P>::sub(v[1], v[2])), KS3);
+    const C m = A::mk(A::sub(A::re(v[0]), A::half(A::re(s))), A::sub(A::im(v[0]), A::half(A::im(s))));
+    v[0] = Cx<P>::add(v[0], s);
+    v[1] = Cx<P>::add(m, d);
+    v[2] = Cx<P>::sub(m, d);
   }
 };
 
-template <typename T, bool INV> struct Dft<T, 4, INV> {
-  using C = typename CxT<T>::type;
+template <typename P, bool INV> struct Dft<P, 4, INV> {
+  using C = typename Ar<P>::C;
   __device__ __forceinline__ static void run(C* v) {
-    C a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-    C c = cadd(v[1], v[3]), d = mul_mi<INV>(csub(v[1], v[3]));
-    v[0] = cadd(a, c);
-    v[2] = csub(a, c);
-    v[1] = cadd(b, d);
-    v[3] = csub(b, d);
+    const C a = Cx<P>::add(v[0], v[2]), b = Cx<P>::sub(v[0], v[2]);
+    const C c = Cx<P>::add(v[1], v[3]), d = Cx<P>::template mmi<INV>(Cx<P>::sub(v[1], v[3]));
+    v[0] = Cx<P>::add(a, c);
+    v[2] = Cx<P>::sub(a, c);
+    v[1] = Cx<P>::add(b, d);
+    v[3] = Cx<P>::sub(b, d);
   }
 };
 
-template <typename T, bool INV> struct Dft<T, 5, INV> {
-  using C = typename CxT<T>::type;
+template <typename P, bool INV> struct Dft<P, 5, INV> {
+  using C = typename Ar<P>::C;
   __device__ __forceinline__ static void run(C* v) {
-    C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
-    C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
-    C x0 = v[0];
-    C r1 = {x0.x + T(K_C1) * a1.x + T(K_C2) * a2.x, x0.y + T(K_C1) * a1.y + T(K_C2) * a2.y};
-    C r2 = {x0.x + T(K_C2) * a1.x + T(K_C1) * a2.x, x0.y + T(K_C2) * a1.y + T(K_C1) * a2.y};
-    C j1 = mul_mi<INV>(C{T(K_S1) * b1.x + T(K_S2) * b2.x, T(K_S1) * b1.y + T(K_S2) * b2.y});
-    C j2 = mul_mi<INV>(C{T(K_S2) * b1.x - T(K_S1) * b2.x, T(K_S2) * b1.y - T(K_S1) * b2.y});
-    v[0] = cadd(x0, cadd(a1, a2));
-    v[1] = cadd(r1, j1);
-    v[4] = csub(r1, j1);
-    v[2] = cadd(r2, j2);
-    v[3] = csub(r2, j2);
+    const C a1 = Cx<P>::add(v[1], v[4]), b1 = Cx<P>::sub(v[1], v[4]);
+    const C a2 = Cx<P>::add(v[2], v[3]), b2 = Cx<P>::sub(v[2], v[3]);
+    const C x0 = v[0];
+    const C r1 = Cx<P>::add(x0, Cx<P>::add(Cx<P>::mulk(a1, KC1), Cx<P>::mulk(a2, KC2)));
+    const C r2 = Cx<P>::add(x0, Cx<P>::add(Cx<P>::mulk(a1, KC2), Cx<P>::mulk(a2, KC1)));
+    const C j1 = Cx<P>::template mmi<INV>(Cx<P>::add(Cx<P>::mulk(b1, KS1), Cx<P>::mulk(b2, KS2)));
+    const C j2 = Cx<P>::template mmi<INV>(Cx<P>::sub(Cx<P>::mulk(b1, KS2), Cx<P>::mulk(b2, KS1)));
+    v[0] = Cx<P>::add(x0, Cx<P>::add(a1, a2));
+    v[1] = Cx<P>::add(r1, j1);
+    v[4] = Cx<P>::sub(r1, j1);
+    v[2] = Cx<P>::add(r2, j2);
+    v[3] = Cx<P>::sub(r2, j2);
   }
 };
 
-template <typename T, bool INV> struct Dft<T, 8, INV> {
-  using C = typename CxT<T>::type;
+template <typename P, bool INV> struct Dft<P, 8, INV> {
+  using A = Ar<P>;
+  using C = typename A::C;
   __device__ __forceinline__ static void run(C* v) {
     C e[4] = {v[0], v[2], v[4], v[6]};
     C o[4] = {v[1], v[3], v[5], v[7]};
-    Dft<T, 4, INV>::run(e);
-    Dft<T, 4, INV>::run(o);
-    // o_p *= exp(-+2 pi i p / 8)
-    const T r = T(K_R2);
-    o[1] = INV ? C{r * (o[1].x - o[1].y), r * (o[1].x + o[1].y)} : C{r * (o[1].x + o[1].y), r * (o[1].y - o[1].x)};
-    o[2] = mul_mi<INV>(o[2]);
-    o[3] = INV ? C{-r * (o[3].x + o[3].y), r * (o[3].x - o[3].y)} : C{r * (o[3].y - o[3].x), -r * (o[3].x + o[3].y)};
+    Dft<P, 4, INV>::run(e);
+    Dft<P, 4, INV>::run(o);
+    // o_p *= exp(-+2 pi i p / 8): (1 -+ i)/sqrt2, -+i, (-1 -+ i)/sqrt2
+    {
+      const C t = Cx<P>::template mmi<INV>(o[1]);                 // -+i o1
+      o[1] = Cx<P>::mulk(Cx<P>::add(o[1], t), KR2);                // (1 -+ i) o1 / sqrt2
+    }
+    o[2] = Cx<P>::template mmi<INV>(o[2]);
+    {
+      const C t = Cx<P>::template mmi<INV>(o[3]);
+      o[3] = Cx<P>::mulk(Cx<P>::sub(t, o[3]), KR2);                // (-1 -+ i) o3 / sqrt2
+    }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      v[p] = cadd(e[p], o[p]);
-      v[p + 4] = csub(e[p], o[p]);
+      v[p] = Cx<P>::add(e[p], o[p]);
+      v[p + 4] = Cx<P>::sub(e[p], o[p]);
     }
   }
 };
@@ -120,11 +268,11 @@ template <typename T, bool INV> struct Dft<T, 8, INV> {
 // One Stockham pass of radix R over a length-L signal: reads `in`, writes `out`.
 // Butterfly j (< L/R) takes in[j + q L/R], applies the twiddle of its position
 // k = j mod Ns inside the current sub-transform, and writes out[(j-k) R + k + q Ns].
-template <typename T, int R, bool INV>
-__device__ __forceinline__ void stockham_pass(const typename CxT<T>::type* __restrict__ in,
-                                              typename CxT<T>::type* __restrict__ out, int L, int Ns,
-                                              const typename CxT<T>::type* __restrict__ tw) {
-  using C = typename CxT<T>::type;
+template <typename P, int R, bool INV>
+__device__ __forceinline__ void stockham_pass(const typename Ar<P>::C* __restrict__ in, typename Ar<P>::C* __restrict__ out,
+                                              int L, int Ns, const typename Ar<P>::C* __restrict__ tw) {
+  using A = Ar<P>;
+  using C = typename A::C;
   const int nb = L / R;
   const int tw_step = L / (Ns * R);
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
@@ -136,11 +284,11 @@ __device__ __forceinline__ void stockham_pass(const typename CxT<T>::type* __res
 #pragma unroll
       for (int q = 1; q < R; ++q) {
         C w = tw[q * k * tw_step];
-        if (INV) w.y = -w.y;
-        v[q] = cmul(v[q], w);
+        if (INV) w = A::conj(w);
+        v[q] = A::cmul(v[q], w);
       }
     }
-    Dft<T, R, INV>::run(v);
+    Dft<P, R, INV>::run(v);
     const int base = (j - k) * R + k;
 #pragma unroll
     for (int q = 0; q < R; ++q) out[base + q * Ns] = v[q];
@@ -148,10 +296,10 @@ __device__ __forceinline__ void stockham_pass(const typename CxT<T>::type* __res
 }
 
 // Full FFT of the signal in buf0; returns the buffer that holds the result.
-template <typename T, bool INV>
-__device__ typename CxT<T>::type* fft_smem(typename CxT<T>::type* buf0, typename CxT<T>::type* buf1,
-                                           const FftPlan& plan, const typename CxT<T>::type* __restrict__ tw) {
-  using C = typename CxT<T>::type;
+template <typename P, bool INV>
+__device__ typename Ar<P>::C* fft_smem(typename Ar<P>::C* buf0, typename Ar<P>::C* buf1, const FftPlan& plan,
+                                       const typename Ar<P>::C* __restrict__ tw) {
+  using C = typename Ar<P>::C;
   C* in = buf0;
   C* out = buf1;
   int Ns = 1;
@@ -159,11 +307,11 @@ __device__ typename CxT<T>::type* fft_smem(typename CxT<T>::type* buf0, typename
     const int R = plan.rad[p];
     __syncthreads();
     switch (R) {
-      case 2: stockham_pass<T, 2, INV>(in, out, plan.L, Ns, tw); break;
-      case 3: stockham_pass<T, 3, INV>(in, out, plan.L, Ns, tw); break;
-      case 4: stockham_pass<T, 4, INV>(in, out, plan.L, Ns, tw); break;
-      case 5: stockham_pass<T, 5, INV>(in, out, plan.L, Ns, tw); break;
-      default: stockham_pass<T, 8, INV>(in, out, plan.L, Ns, tw); break;
+      case 2: stockham_pass<P, 2, INV>(in, out, plan.L, Ns, tw); break;
+      case 3: stockham_pass<P, 3, INV>(in, out, plan.L, Ns, tw); break;
+      case 4: stockham_pass<P, 4, INV>(in, out, plan.L, Ns, tw); break;
+      case 5: stockham_pass<P, 5, INV>(in, out, plan.L, Ns, tw); break;
+      default: stockham_pass<P, 8, INV>(in, out, plan.L, Ns, tw); break;
     }
     Ns *= R;
     C* t = in;
@@ -174,38 +322,66 @@ __device__ typename CxT<T>::type* fft_smem(typename CxT<T>::type* buf0, typename
   return in;
 }
 
-template <typename T> __device__ __forceinline__ T load_real(const void* p, int64_t i);
-template <> __device__ __forceinline__ double load_real<double>(const void* p, int64_t i) {
-  return __ldg(static_cast<const double*>(p) + i);
-}
-template <> __device__ __forceinline__ float load_real<float>(const void* p, int64_t i) {
-  return __ldg(static_cast<const float*>(p) + i);
+// --- loads and stores with the phase casts --------------------------------
+
+template <typename P, typename Tin>
+__device__ __forceinline__ typename Ar<P>::R load_real(const void* p, int64_t i, bool pad_single) {
+  const Tin x = __ldg(static_cast<const Tin*>(p) + i);
+  if (pad_single) return Ar<P>::from_f((float)x);
+  if constexpr (sizeof(Tin) == 8) return Ar<P>::from_d((double)x);
+  else return Ar<P>::from_f((float)x);
 }
 
-// Store one complex value (re, im) computed in precision T into format fmt.
-template <typename T>
-__device__ __forceinline__ void store_cx(void* X, int64_t i, int fmt, T re, T im) {
+// store one complex value (re, im) of precision P into format fmt
+template <typename P>
+__device__ __forceinline__ void store_cx(void* X, int64_t i, int fmt, typename Ar<P>::R re, typename Ar<P>::R im) {
+  using A = Ar<P>;
   if (fmt == FMT_C128) {
-    static_cast<double2*>(X)[i] = make_double2((double)re, (double)im);
+    static_cast<double2*>(X)[i] = make_double2(A::to_d(re), A::to_d(im));
   } else if (fmt == FMT_C64) {
-    static_cast<float2*>(X)[i] = make_float2((float)re, (float)im);
+    static_cast<float2*>(X)[i] = make_float2(A::to_f(re), A::to_f(im));
   } else {
-    const float hr = (float)re, hi = (float)im;
-    const float lr = (float)((double)re - (double)hr), li = (float)((double)im - (double)hi);
-    static_cast<float4*>(X)[i] = make_float4(hr, hi, lr, li);
+    if constexpr (std::is_same<P, double>::value) {
+      // FP64 value -> hi/lo pair
+      const double r = A::to_d(re), m = A::to_d(im);
+      const float hr = (float)r, hm = (float)m;
+      static_cast<float4*>(X)[i] = make_float4(hr, hm, (float)(r - (double)hr), (float)(m - (double)hm));
+    } else if constexpr (std::is_same<P, DFP>::value) {
+      static_cast<float4*>(X)[i] = Ar<DFP>::mk(re, im);
+    } else {
+      static_cast<float4*>(X)[i] = make_float4(A::to_f(re), A::to_f(im), 0.f, 0.f);
+    }
   }
 }
 
-__device__ __forceinline__ double2 load_cx(const void* X, int64_t i, int fmt) {
-  if (fmt == FMT_C128) return __ldg(static_cast<const double2*>(X) + i);
-  const float2 v = __ldg(static_cast<const float2*>(X) + i);
-  return make_double2(v.x, v.y);
+// load one complex value stored in format fmt into precision P
+template <typename P>
+__device__ __forceinline__ typename Ar<P>::C load_cx(const void* X, int64_t i, int fmt) {
+  using A = Ar<P>;
+  if (fmt == FMT_C128) {
+    const double2 v = __ldg(static_cast<const double2*>(X) + i);
+    return A::mk(A::from_d(v.x), A::from_d(v.y));
+  }
+  if (fmt == FMT_C64) {
+    const float2 v = __ldg(static_cast<const float2*>(X) + i);
+    return A::mk(A::from_f(v.x), A::from_f(v.y));
+  }
+  const float4 v = __ldg(static_cast<const float4*>(X) + i);
+  if constexpr (std::is_same<P, DFP>::value) {
+    return v;
+  } else if constexpr (std::is_same<P, double>::value) {
+    return A::mk((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  } else {
+    return A::mk(__fadd_rn(v.x, v.z), __fadd_rn(v.y, v.w));
+  }
 }
 
 // Forward: pad + real FFT of channel pairs; grid (pairs, K).
-template <typename Tin, typename T>
+template <typename Tin, typename P>
 __global__ void __launch_bounds__(256) rfft_fwd_kernel(FwdDesc d) {
-  using C = typename CxT<T>::type;
+  using A = Ar<P>;
+  using C = typename A::C;
+  using R = typename A::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + d.plan.L;
@@ -223,55 +399,57 @@ __global__ void __launch_bounds__(256) rfft_fwd_kernel(FwdDesc d) {
 
   if (!has_a) {  // a pair of padding columns: exact zeros
     for (int w = threadIdx.x; w < Nf; w += blockDim.x) {
-      store_cx<T>(d.X, Xo + w * d.X_ld_w + ca, d.fmt, T(0), T(0));
-      if (write_b) store_cx<T>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, T(0), T(0));
+      store_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.fmt, A::zero(), A::zero());
+      if (write_b) store_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, A::zero(), A::zero());
     }
     return;
   }
   // phase 1: load, cast to the pad precision, then to the FFT precision; zero pad
   for (int t = threadIdx.x; t < L; t += blockDim.x) {
-    T va = T(0), vb = T(0);
+    R va = A::zero(), vb = A::zero();
     if (t < d.Nt) {
-      Tin a = load_real<Tin>(d.x, xo + t * d.x_ld_t + ca);
-      Tin bb = has_b ? load_real<Tin>(d.x, xo + t * d.x_ld_t + cb) : Tin(0);
-      if (d.pad_single) {
-        a = (Tin)(float)a;
-        bb = (Tin)(float)bb;
-      }
-      va = (T)a;
-      vb = (T)bb;
+      va = load_real<P, Tin>(d.x, xo + t * d.x_ld_t + ca, d.pad_single);
+      if (has_b) vb = load_real<P, Tin>(d.x, xo + t * d.x_ld_t + cb, d.pad_single);
     }
-    buf0[t] = C{va, vb};
+    buf0[t] = A::mk(va, vb);
   }
   // phase 2: complex FFT of z = x_a + i x_b
   const C* tw = static_cast<const C*>(d.tw);
-  const C* Z = fft_smem<T, false>(buf0, buf1, d.plan, tw);
+  const C* Z = fft_smem<P, false>(buf0, buf1, d.plan, tw);
   // split: X_a = (Z_w + conj Z_{L-w}) / 2,  X_b = (Z_w - conj Z_{L-w}) / (2i)
   for (int w = threadIdx.x; w < Nf; w += blockDim.x) {
     const C z = Z[w];
     const C zc = Z[w == 0 ? 0 : L - w];
-    const T ar = T(0.5) * (z.x + zc.x), ai = T(0.5) * (z.y - zc.y);
-    const T br = T(0.5) * (z.y + zc.y), bi = T(0.5) * (zc.x - z.x);
-    store_cx<T>(d.X, Xo + w * d.X_ld_w + ca, d.fmt, ar, ai);
+    const R ar = A::half(A::add(A::re(z), A::re(zc)));
+    const R ai = A::half(A::sub(A::im(z), A::im(zc)));
+    store_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.fmt, ar, ai);
     if (write_b) {
-      if (has_b) store_cx<T>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, br, bi);
-      else store_cx<T>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, T(0), T(0));
+      if (has_b) {
+        const R br = A::half(A::add(A::im(z), A::im(zc)));
+        const R bi = A::half(A::sub(A::re(zc), A::re(z)));
+        store_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, br, bi);
+      } else {
+        store_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, A::zero(), A::zero());
+      }
     }
   }
 }
 
-template <typename T> __device__ __forceinline__ void store_real(void* y, int64_t i, T v);
-template <> __device__ __forceinline__ void store_real<double>(void* y, int64_t i, double v) {
-  static_cast<double*>(y)[i] = v;
-}
-template <> __device__ __forceinline__ void store_real<float>(void* y, int64_t i, float v) {
-  static_cast<float*>(y)[i] = v;
+template <typename Tout, typename P>
+__device__ __forceinline__ void store_real(void* y, int64_t i, typename Ar<P>::R v, bool unpad_single) {
+  if (unpad_single || sizeof(Tout) == 4) {
+    static_cast<Tout*>(y)[i] = (Tout)Ar<P>::to_f(v);
+  } else {
+    static_cast<Tout*>(y)[i] = (Tout)Ar<P>::to_d(v);
+  }
 }
 
 // Inverse: Hermitian assembly + inverse complex FFT + unpad; grid (pairs, K).
-template <typename T, typename Tout>
+template <typename P, typename Tout>
 __global__ void __launch_bounds__(256) irfft_inv_kernel(InvDesc d) {
-  using C = typename CxT<T>::type;
+  using A = Ar<P>;
+  using C = typename A::C;
+  using R = typename A::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + d.plan.L;
@@ -284,28 +462,25 @@ __global__ void __launch_bounds__(256) irfft_inv_kernel(InvDesc d) {
   // Z_w = X_a(w) + i X_b(w) over the full circle, X(L-w) = conj X(w);
   // the DC and Nyquist terms of a real signal's spectrum are taken as real.
   for (int w = threadIdx.x; w < Nf; w += blockDim.x) {
-    double2 a = load_cx(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt);
-    double2 bb = has_b ? load_cx(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : make_double2(0.0, 0.0);
-    const T ax = (T)a.x, ay = (T)a.y, bx = (T)bb.x, by = (T)bb.y;
+    const C a = load_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt);
+    const C bb = has_b ? load_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : A::mk(A::zero(), A::zero());
     if (w == 0 || w == Nf - 1) {
-      buf0[w] = C{ax, bx};
+      buf0[w] = A::mk(A::re(a), A::re(bb));
     } else {
-      buf0[w] = C{ax - by, ay + bx};
-      buf0[L - w] = C{ax + by, bx - ay};
+      buf0[w] = A::mk(A::sub(A::re(a), A::im(bb)), A::add(A::im(a), A::re(bb)));
+      buf0[L - w] = A::mk(A::add(A::re(a), A::im(bb)), A::sub(A::re(bb), A::im(a)));
     }
   }
   const C* tw = static_cast<const C*>(d.tw);
-  const C* z = fft_smem<T, true>(buf0, buf1, d.plan, tw);
-  const T scale = T(1) / T(L);
+  const C* z = fft_smem<P, true>(buf0, buf1, d.plan, tw);
+  const Kc inv_L{d.inv_L, d.inv_L_hi, d.inv_L_lo};
   for (int t = threadIdx.x; t < d.Nt; t += blockDim.x) {
-    T va = z[t].x * scale, vb = z[t].y * scale;
-    if (d.unpad_single) {
-      va = (T)(float)va;
-      vb = (T)(float)vb;
-    }
+    const C zt = z[t];
+    const R va = A::mulk(A::re(zt), inv_L);
+    const R vb = A::mulk(A::im(zt), inv_L);
     const int64_t yo = b * d.y_ld_b + t * d.y_ld_t;
-    store_real<Tout>(d.y, yo + ca, (Tout)va);
-    if (has_b) store_real<Tout>(d.y, yo + cb, (Tout)vb);
+    store_real<Tout, P>(d.y, yo + ca, va, d.unpad_single);
+    if (has_b) store_real<Tout, P>(d.y, yo + cb, vb, d.unpad_single);
   }
 }
 
@@ -315,51 +490,58 @@ cudaError_t prep(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
+template <typename Tin, typename P>
+cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
+  const int pairs = d.rows * ((d.out_cols + 1) / 2);
+  dim3 grid(pairs, d.K);
+  const size_t smem = 2 * (size_t)d.plan.L * sizeof(typename Ar<P>::C);
+  cudaError_t e = prep(rfft_fwd_kernel<Tin, P>, smem);
+  if (e != cudaSuccess) return e;
+  rfft_fwd_kernel<Tin, P><<<grid, 256, smem, s>>>(d);
+  return cudaGetLastError();
+}
+
+template <typename P, typename Tout>
+cudaError_t inv_launch(const InvDesc& d, cudaStream_t s) {
+  dim3 grid((d.cols + 1) / 2, d.K);
+  const size_t smem = 2 * (size_t)d.plan.L * sizeof(typename Ar<P>::C);
+  cudaError_t e = prep(irfft_inv_kernel<P, Tout>, smem);
+  if (e != cudaSuccess) return e;
+  irfft_inv_kernel<P, Tout><<<grid, 256, smem, s>>>(d);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-size_t fft_smem_bytes(int L, bool fft_f32) { return 2 * (size_t)L * (fft_f32 ? sizeof(float2) : sizeof(double2)); }
+size_t fft_smem_bytes(int L, int prec) { return 2 * (size_t)L * (prec == FFT_F32 ? sizeof(float2) : 16); }
 
-int fft_max_length(bool fft_f32) {
+int fft_max_length(int prec) {
   const size_t cap = 227 * 1024;
-  return (int)(cap / (2 * (fft_f32 ? sizeof(float2) : sizeof(double2))));
+  return (int)(cap / (2 * (prec == FFT_F32 ? sizeof(float2) : 16)));
 }
 
-cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, bool fft_f32, cudaStream_t s) {
-  const int pairs = d.rows * ((d.out_cols + 1) / 2);
-  if (pairs == 0 || d.K == 0) return cudaSuccess;
-  dim3 grid(pairs, d.K);
-  const size_t smem = fft_smem_bytes(d.plan.L, fft_f32);
-  cudaError_t e;
-#define FWD_CASE(TIN, T)                                           \
-  do {                                                             \
-    if ((e = prep(rfft_fwd_kernel<TIN, T>, smem)) != cudaSuccess) return e; \
-    rfft_fwd_kernel<TIN, T><<<grid, 256, smem, s>>>(d);            \
-  } while (0)
-  if (!in_f32 && !fft_f32) FWD_CASE(double, double);
-  else if (!in_f32 && fft_f32) FWD_CASE(double, float);
-  else if (in_f32 && !fft_f32) FWD_CASE(float, double);
-  else FWD_CASE(float, float);
-#undef FWD_CASE
-  return cudaGetLastError();
+cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, int prec, cudaStream_t s) {
+  if (d.rows == 0 || d.out_cols == 0 || d.K == 0) return cudaSuccess;
+  if (!in_f32) {
+    if (prec == FFT_F64) return fwd_launch<double, double>(d, s);
+    if (prec == FFT_DF) return fwd_launch<double, DFP>(d, s);
+    return fwd_launch<double, float>(d, s);
+  }
+  if (prec == FFT_F64) return fwd_launch<float, double>(d, s);
+  if (prec == FFT_DF) return fwd_launch<float, DFP>(d, s);
+  return fwd_launch<float, float>(d, s);
 }
 
-cudaError_t launch_irfft_inv(const InvDesc& d, bool fft_f32, bool out_f32, cudaStream_t s) {
-  const int pairs = (d.cols + 1) / 2;
-  if (pairs == 0 || d.K == 0) return cudaSuccess;
-  dim3 grid(pairs, d.K);
-  const size_t smem = fft_smem_bytes(d.plan.L, fft_f32);
-  cudaError_t e;
-#define INV_CASE(T, TOUT)                                            \
-  do {                                                               \
-    if ((e = prep(irfft_inv_kernel<T, TOUT>, smem)) != cudaSuccess) return e; \
-    irfft_inv_kernel<T, TOUT><<<grid, 256, smem, s>>>(d);            \
-  } while (0)
-  if (!fft_f32 && !out_f32) INV_CASE(double, double);
-  else if (!fft_f32 && out_f32) INV_CASE(double, float);
-  else if (fft_f32 && !out_f32) INV_CASE(float, double);
-  else INV_CASE(float, float);
-#undef INV_CASE
-  return cudaGetLastError();
+cudaError_t launch_irfft_inv(const InvDesc& d, int prec, bool out_f32, cudaStream_t s) {
+  if (d.cols == 0 || d.K == 0) return cudaSuccess;
+  if (!out_f32) {
+    if (prec == FFT_F64) return inv_launch<double, double>(d, s);
+    if (prec == FFT_DF) return inv_launch<DFP, double>(d, s);
+    return inv_launch<float, double>(d, s);
+  }
+  if (prec == FFT_F64) return inv_launch<double, float>(d, s);
+  if (prec == FFT_DF) return inv_launch<DFP, float>(d, s);
+  return inv_launch<float, float>(d, s);
 }
 
 }  // namespace fftmv

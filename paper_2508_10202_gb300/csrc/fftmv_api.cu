@@ -100,6 +100,7 @@ struct fftmv_op {
   FftPlan plan{};
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
+  float4* twdf = nullptr;     // twiddles as FP32 hi/lo pairs
   double2* fhat64 = nullptr;  // master F-hat [Nf][Nd][ldn], FP64
   float4* fhat_df = nullptr;  // FP32 hi/lo pairs
   float2* fhat32 = nullptr;   // FP32
@@ -141,12 +142,20 @@ int check_prec(const fftmv_precision* p) {
     return fail(FFTMV_EINVAL, "gemv_mode %d unknown", p->gemv_mode);
   if (p->gemv_mode == FFTMV_GEMV_F64X2F32 && p->gemv != FFTMV_F64)
     return fail(FFTMV_EINVAL, "gemv_mode F64X2F32 needs an FP64 GEMV phase");
+  if (p->fft_mode != FFTMV_GEMV_NATIVE && p->fft_mode != FFTMV_GEMV_F64X2F32)
+    return fail(FFTMV_EINVAL, "fft_mode %d unknown", p->fft_mode);
   return FFTMV_OK;
 }
 
 int gemv_kind(const fftmv_precision& p) {
   if (p.gemv == FFTMV_F32) return GEMV_F32;
   return p.gemv_mode == FFTMV_GEMV_F64X2F32 ? GEMV_DF : GEMV_F64;
+}
+
+// arithmetic of an FFT phase from its precision letter and the FP64 mode
+int fft_prec(int32_t phase, int32_t mode) {
+  if (phase == FFTMV_F32) return FFT_F32;
+  return mode == FFTMV_GEMV_F64X2F32 ? FFT_DF : FFT_F64;
 }
 
 const void* fhat_for(const fftmv_op* op, int kind) {
@@ -156,6 +165,7 @@ const void* fhat_for(const fftmv_op* op, int kind) {
 void release(fftmv_op* op) {
   cudaFree(op->tw64);
   cudaFree(op->tw32);
+  cudaFree(op->twdf);
   cudaFree(op->fhat64);
   cudaFree(op->fhat_df);
   cudaFree(op->fhat32);
@@ -189,6 +199,73 @@ CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
   c.in_hat = align256((size_t)K * op->Nf * c.in_ld * fmt_bytes(c.in_fmt));
   c.out_hat = align256((size_t)K * op->Nf * c.out_ld * fmt_bytes(c.out_fmt));
   return c;
+}
+
+// The three kernel groups of one call (Section 2.4): pad+FFT -> spectrum
+// in_hat, block matvec -> out_hat, IFFT+unpad -> y.  ev, when given, holds four
+// events recorded around them.
+cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, const void* x, void* y, void* in_hat,
+                          void* out_hat, int64_t K, int io, cudaStream_t s, cudaEvent_t* ev) {
+  const fftmv_precision& p = op->prec[which];
+  const int fprec = fft_prec(p.fft, p.fft_mode), iprec = fft_prec(p.ifft, p.fft_mode);
+  const bool fwd = which == FFTMV_FORWARD;
+  if (ev) cudaEventRecord(ev[0], s);
+  FwdDesc f{};
+  f.plan = op->plan;
+  f.tw = fprec == FFT_F32 ? (const void*)op->tw32 : fprec == FFT_DF ? (const void*)op->twdf : (const void*)op->tw64;
+  f.x = x;
+  f.X = in_hat;
+  f.Nt = (int)op->Nt;
+  f.rows = 1;
+  f.cols = (int)c.Cin;
+  f.out_cols = (int)c.in_ld;
+  f.K = (int)K;
+  f.x_ld_t = c.Cin;
+  f.x_ld_row = 0;
+  f.x_ld_b = op->Nt * c.Cin;
+  f.X_ld_w = c.in_ld;
+  f.X_ld_row = 0;
+  f.X_ld_b = op->Nf * c.in_ld;
+  f.fmt = c.in_fmt;
+  f.pad_single = p.pad == FFTMV_F32;
+  cudaError_t e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fprec, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess) {
+    GemvDesc g{};
+    g.F = fhat_for(op, c.kind);
+    g.x = in_hat;
+    g.y = out_hat;
+    g.Nf = (int)op->Nf;
+    g.Nd = (int)op->Nd;
+    g.ldn = (int)op->ldn;
+    g.K = (int)K;
+    g.x_ld_b = op->Nf * c.in_ld;
+    g.y_ld_b = op->Nf * c.out_ld;
+    e = fwd ? launch_gemv_n(c.kind, g, s) : launch_gemv_h(c.kind, g, s);
+  }
+  if (ev) cudaEventRecord(ev[2], s);
+  if (e == cudaSuccess) {
+    InvDesc v{};
+    v.plan = op->plan;
+    v.tw = iprec == FFT_F32 ? (const void*)op->tw32 : iprec == FFT_DF ? (const void*)op->twdf : (const void*)op->tw64;
+    v.X = out_hat;
+    v.y = y;
+    v.Nt = (int)op->Nt;
+    v.cols = (int)c.Cout;
+    v.K = (int)K;
+    v.X_ld_w = c.out_ld;
+    v.X_ld_b = op->Nf * c.out_ld;
+    v.y_ld_t = c.Cout;
+    v.y_ld_b = op->Nt * c.Cout;
+    v.in_fmt = c.out_fmt;
+    v.unpad_single = p.unpad == FFTMV_F32;
+    v.inv_L = 1.0 / (double)op->L;
+    v.inv_L_hi = (float)v.inv_L;
+    v.inv_L_lo = (float)(v.inv_L - (double)v.inv_L_hi);
+    e = launch_irfft_inv(v, iprec, io == FFTMV_IO_F32, s);
+  }
+  if (ev) cudaEventRecord(ev[3], s);
+  return e;
 }
 
 int run_matvec(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io, void* stream) {
@@ -232,10 +309,6 @@ int run_matvec(fftmv_op* op, int which, const void* in, void* out, int64_t K, in
   }
   if (!out_dev) y = out_hat + c.out_hat + stage_in;
 
-  const fftmv_precision& p = op->prec[which];
-  const bool fft32 = p.fft == FFTMV_F32, ifft32 = p.ifft == FFTMV_F32;
-  const bool fwd = which == FFTMV_FORWARD;
-
   TimingSet ts{};
   bool timed = false;
   if (op->timing) {
@@ -246,70 +319,14 @@ int run_matvec(fftmv_op* op, int which, const void* in, void* out, int64_t K, in
       timed = true;
     } else {
       timed = true;
-      for (auto& e : ts.ev)
-        if (cudaEventCreate(&e) != cudaSuccess) timed = false;
+      for (auto& ev : ts.ev)
+        if (cudaEventCreate(&ev) != cudaSuccess) timed = false;
       cudaGetLastError();
     }
     ts.which = which;
   }
-
-  cudaError_t e = cudaSuccess;
-  if (timed) cudaEventRecord(ts.ev[0], s);
-  {  // phases 1-2
-    FwdDesc f{};
-    f.plan = op->plan;
-    f.tw = fft32 ? (const void*)op->tw32 : (const void*)op->tw64;
-    f.x = x;
-    f.X = in_hat;
-    f.Nt = (int)op->Nt;
-    f.rows = 1;
-    f.cols = (int)c.Cin;
-    f.out_cols = (int)c.in_ld;
-    f.K = (int)K;
-    f.x_ld_t = c.Cin;
-    f.x_ld_row = 0;
-    f.x_ld_b = op->Nt * c.Cin;
-    f.X_ld_w = c.in_ld;
-    f.X_ld_row = 0;
-    f.X_ld_b = op->Nf * c.in_ld;
-    f.fmt = c.in_fmt;
-    f.pad_single = p.pad == FFTMV_F32;
-    e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fft32, s);
-  }
-  if (timed) cudaEventRecord(ts.ev[1], s);
-  if (e == cudaSuccess) {  // phase 3
-    GemvDesc g{};
-    g.F = fhat_for(op, c.kind);
-    g.x = in_hat;
-    g.y = out_hat;
-    g.Nf = (int)op->Nf;
-    g.Nd = (int)op->Nd;
-    g.ldn = (int)op->ldn;
-    g.K = (int)K;
-    g.x_ld_b = op->Nf * c.in_ld;
-    g.y_ld_b = op->Nf * c.out_ld;
-    e = fwd ? launch_gemv_n(c.kind, g, s) : launch_gemv_h(c.kind, g, s);
-  }
-  if (timed) cudaEventRecord(ts.ev[2], s);
-  if (e == cudaSuccess) {  // phases 4-5
-    InvDesc v{};
-    v.plan = op->plan;
-    v.tw = ifft32 ? (const void*)op->tw32 : (const void*)op->tw64;
-    v.X = out_hat;
-    v.y = y;
-    v.Nt = (int)op->Nt;
-    v.cols = (int)c.Cout;
-    v.K = (int)K;
-    v.X_ld_w = c.out_ld;
-    v.X_ld_b = op->Nf * c.out_ld;
-    v.y_ld_t = c.Cout;
-    v.y_ld_b = op->Nt * c.Cout;
-    v.in_fmt = c.out_fmt;
-    v.unpad_single = p.unpad == FFTMV_F32;
-    e = launch_irfft_inv(v, ifft32, io == FFTMV_IO_F32, s);
-  }
+  cudaError_t e = launch_phases(op, which, c, x, y, in_hat, out_hat, K, io, s, timed ? ts.ev : nullptr);
   if (timed) {
-    cudaEventRecord(ts.ev[3], s);
     std::lock_guard<std::mutex> g(op->mu);
     op->pending.push_back(ts);
   }
@@ -336,9 +353,9 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
   if (Nt < 1 || Nd < 1 || Nm < 1) return fail(FFTMV_EINVAL, "sizes must be >= 1 (Nt=%lld Nd=%lld Nm=%lld)",
                                               (long long)Nt, (long long)Nd, (long long)Nm);
   const int64_t L = choose_length(Nt);
-  if (L > fft_max_length(false))
+  if (L > fft_max_length(FFT_F64))
     return fail(FFTMV_EUNSUPPORTED, "FFT length %lld for Nt=%lld exceeds the shared-memory FFT limit %d",
-                (long long)L, (long long)Nt, fft_max_length(false));
+                (long long)L, (long long)Nt, fft_max_length(FFT_F64));
   const int64_t ldn = (Nm + 7) / 8 * 8;
   const int64_t Nf = L / 2 + 1;
   if (Nd * ldn > INT32_MAX || ldn > INT32_MAX / 2 || Nf * Nd > INT32_MAX)
@@ -353,7 +370,8 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
   op->Nf = Nf;
   op->ldn = ldn;
   op->plan = make_plan(L);
-  for (auto& p : op->prec) p = fftmv_precision{FFTMV_F64, FFTMV_F64, FFTMV_F64, FFTMV_F64, FFTMV_F64, FFTMV_GEMV_NATIVE};
+  for (auto& p : op->prec)
+    p = fftmv_precision{FFTMV_F64, FFTMV_F64, FFTMV_F64, FFTMV_F64, FFTMV_F64, FFTMV_GEMV_NATIVE, FFTMV_GEMV_NATIVE};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   auto bail = [&](int code) {
@@ -368,15 +386,21 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
   // twiddles exp(-2 pi i j / L), evaluated in long double and rounded once
   std::vector<double2> tw((size_t)L);
   std::vector<float2> tw32((size_t)L);
+  std::vector<float4> twdf((size_t)L);
   for (int64_t j = 0; j < L; ++j) {
     const long double a = -2.0L * 3.141592653589793238462643383279502884L * (long double)j / (long double)L;
-    tw[j] = make_double2((double)cosl(a), (double)sinl(a));
-    tw32[j] = make_float2((float)cosl(a), (float)sinl(a));
+    const long double c = cosl(a), sn = sinl(a);
+    tw[j] = make_double2((double)c, (double)sn);
+    tw32[j] = make_float2((float)c, (float)sn);
+    const float ch = (float)c, sh = (float)sn;
+    twdf[j] = make_float4(ch, sh, (float)(c - (long double)ch), (float)(sn - (long double)sh));
   }
   if ((rc = cu(cudaMalloc(&op->tw64, L * sizeof(double2)), "cudaMalloc(twiddles)"))) return rc;
   if ((rc = cu(cudaMalloc(&op->tw32, L * sizeof(float2)), "cudaMalloc(twiddles)"))) return rc;
   if ((rc = cu(cudaMemcpy(op->tw64, tw.data(), L * sizeof(double2), cudaMemcpyHostToDevice), "twiddle copy"))) return rc;
   if ((rc = cu(cudaMemcpy(op->tw32, tw32.data(), L * sizeof(float2), cudaMemcpyHostToDevice), "twiddle copy"))) return rc;
+  if ((rc = cu(cudaMalloc(&op->twdf, L * sizeof(float4)), "cudaMalloc(twiddles)"))) return rc;
+  if ((rc = cu(cudaMemcpy(op->twdf, twdf.data(), L * sizeof(float4), cudaMemcpyHostToDevice), "twiddle copy"))) return rc;
 
   const size_t fh_elems = (size_t)Nf * Nd * ldn;
   if ((rc = cu(cudaMalloc(&op->fhat64, fh_elems * sizeof(double2)), "cudaMalloc(F-hat)"))) return rc;
@@ -400,7 +424,7 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
     f.X = op->fhat64;
     f.rows = (int)Nd;
     f.x_ld_t = Nd * Nm;
-    if ((rc = cu(launch_rfft_fwd(f, false, false, s), "setup FFT"))) return rc;
+    if ((rc = cu(launch_rfft_fwd(f, false, FFT_F64, s), "setup FFT"))) return rc;
   } else {
     // stage row blocks of the host block column through a bounded device buffer
     const size_t row_bytes = (size_t)Nt * Nm * sizeof(double);
@@ -418,7 +442,7 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
         f.X = op->fhat64 + r0 * ldn;
         f.rows = (int)nr;
         f.x_ld_t = nr * Nm;
-        e = launch_rfft_fwd(f, false, false, s);
+        e = launch_rfft_fwd(f, false, FFT_F64, s);
       }
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) {
@@ -630,56 +654,7 @@ extern "C" int fftmv_apply_noalloc(fftmv_op* op, int which, const void* in, void
   char* in_hat = ws;
   char* out_hat = ws + c.in_hat;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const fftmv_precision& p = op->prec[which];
-  const bool fft32 = p.fft == FFTMV_F32, ifft32 = p.ifft == FFTMV_F32;
-
-  FwdDesc f{};
-  f.plan = op->plan;
-  f.tw = fft32 ? (const void*)op->tw32 : (const void*)op->tw64;
-  f.x = in;
-  f.X = in_hat;
-  f.Nt = (int)op->Nt;
-  f.rows = 1;
-  f.cols = (int)c.Cin;
-  f.out_cols = (int)c.in_ld;
-  f.K = (int)K;
-  f.x_ld_t = c.Cin;
-  f.x_ld_b = op->Nt * c.Cin;
-  f.X_ld_w = c.in_ld;
-  f.X_ld_b = op->Nf * c.in_ld;
-  f.fmt = c.in_fmt;
-  f.pad_single = p.pad == FFTMV_F32;
-  cudaError_t e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fft32, s);
-  if (e == cudaSuccess) {
-    GemvDesc g{};
-    g.F = fhat_for(op, c.kind);
-    g.x = in_hat;
-    g.y = out_hat;
-    g.Nf = (int)op->Nf;
-    g.Nd = (int)op->Nd;
-    g.ldn = (int)op->ldn;
-    g.K = (int)K;
-    g.x_ld_b = op->Nf * c.in_ld;
-    g.y_ld_b = op->Nf * c.out_ld;
-    e = which == FFTMV_FORWARD ? launch_gemv_n(c.kind, g, s) : launch_gemv_h(c.kind, g, s);
-  }
-  if (e == cudaSuccess) {
-    InvDesc v{};
-    v.plan = op->plan;
-    v.tw = ifft32 ? (const void*)op->tw32 : (const void*)op->tw64;
-    v.X = out_hat;
-    v.y = out;
-    v.Nt = (int)op->Nt;
-    v.cols = (int)c.Cout;
-    v.K = (int)K;
-    v.X_ld_w = c.out_ld;
-    v.X_ld_b = op->Nf * c.out_ld;
-    v.y_ld_t = c.Cout;
-    v.y_ld_b = op->Nt * c.Cout;
-    v.in_fmt = c.out_fmt;
-    v.unpad_single = p.unpad == FFTMV_F32;
-    e = launch_irfft_inv(v, ifft32, io == FFTMV_IO_F32, s);
-  }
+  cudaError_t e = launch_phases(op, which, c, in, out, in_hat, out_hat, K, io, s, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "no-alloc matvec kernels");
   return FFTMV_OK;
 }

@@ -22,6 +22,13 @@ enum GemvKind : int {
   GEMV_F32 = 2,   // FP32 F-hat, FP32 FMA
 };
 
+// Arithmetic of an FFT phase.
+enum FftPrec : int {
+  FFT_F64 = 0,  // FP64 FMA
+  FFT_F32 = 1,  // FP32
+  FFT_DF = 2,   // FP64-class double-float on the FP32 pipe
+};
+
 constexpr int kMaxPasses = 16;
 
 // A mixed-radix (2, 3, 4, 5, 8) complex FFT of length L done in shared memory.
@@ -62,8 +69,10 @@ struct InvDesc {
   int K;
   int64_t X_ld_w, X_ld_b;  // complex-element strides
   int64_t y_ld_t, y_ld_b;  // element strides
-  int in_fmt;              // FMT_C128 or FMT_C64
+  int in_fmt;              // FMT_C128, FMT_C64 or FMT_DF
   int unpad_single;        // round the result to FP32 before the output cast
+  double inv_L;            // 1/L in FP64 and as an FP32 hi/lo pair
+  float inv_L_hi, inv_L_lo;
 };
 
 // Per-frequency block matvec (phase 3) for K right-hand sides.
@@ -78,15 +87,15 @@ struct GemvDesc {
   int64_t x_ld_b, y_ld_b;  // complex-element strides between right-hand sides
 };
 
-cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, bool fft_f32, cudaStream_t s);
-cudaError_t launch_irfft_inv(const InvDesc& d, bool fft_f32, bool out_f32, cudaStream_t s);
+cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, int prec, cudaStream_t s);
+cudaError_t launch_irfft_inv(const InvDesc& d, int prec, bool out_f32, cudaStream_t s);
 cudaError_t launch_gemv_n(int kind, const GemvDesc& d, cudaStream_t s);
 cudaError_t launch_gemv_h(int kind, const GemvDesc& d, cudaStream_t s);
 // master FP64 F-hat (double2, n elements) -> kind's storage (DF float4 or F32 float2)
 cudaError_t launch_convert_fhat(int kind, const double2* master, void* out, size_t n, cudaStream_t s);
 
-size_t fft_smem_bytes(int L, bool fft_f32);
-int fft_max_length(bool fft_f32);
+size_t fft_smem_bytes(int L, int prec);
+int fft_max_length(int prec);
 // the input / output format each GEMV kind expects / produces
 int gemv_in_fmt(int kind);
 int gemv_out_fmt(int kind);

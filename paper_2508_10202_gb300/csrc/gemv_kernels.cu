@@ -45,6 +45,13 @@ __device__ __forceinline__ void df_acc(float& hi, float& lo, float p) {
   lo = __fadd_rn(lo, e);
 }
 
+// (hi, lo) -> hi' + lo' with |lo'| <= ulp(hi')/2, exact whatever the magnitudes (TwoSum)
+__device__ __forceinline__ float2 renorm(float hi, float lo) {
+  float s, e;
+  two_sum(hi, lo, s, e);
+  return make_float2(s, e);
+}
+
 // (a_hi, a_lo) + (b_hi, b_lo), renormalised.
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   float s, e;
@@ -134,8 +141,10 @@ struct KindDF {
     return make_float4(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m),
                        __shfl_xor_sync(0xffffffffu, a.z, m), __shfl_xor_sync(0xffffffffu, a.w, m));
   }
+  // FMT_DF: (re_hi, im_hi, re_lo, im_lo), read as is by the double-float FFT
   __device__ __forceinline__ static void store(void* y, int64_t i, Acc a) {
-    static_cast<double2*>(y)[i] = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+    const float2 r = renorm(a.x, a.y), m = renorm(a.z, a.w);
+    static_cast<float4*>(y)[i] = make_float4(r.x, m.x, r.y, m.y);
   }
 };
 
@@ -329,7 +338,7 @@ cudaError_t run_h(const GemvDesc& d, cudaStream_t s) {
 }  // namespace
 
 int gemv_in_fmt(int kind) { return kind == GEMV_F64 ? FMT_C128 : kind == GEMV_DF ? FMT_DF : FMT_C64; }
-int gemv_out_fmt(int kind) { return kind == GEMV_F32 ? FMT_C64 : FMT_C128; }
+int gemv_out_fmt(int kind) { return kind == GEMV_F32 ? FMT_C64 : kind == GEMV_DF ? FMT_DF : FMT_C128; }
 size_t fmt_bytes(int fmt) { return fmt == FMT_C64 ? 8 : 16; }
 
 cudaError_t launch_gemv_n(int kind, const GemvDesc& d, cudaStream_t s) {

@@ -18,14 +18,20 @@ _WHICH = {"F": L.FFTMV_FORWARD, "forward": L.FFTMV_FORWARD, L.FFTMV_FORWARD: L.F
           "F*": L.FFTMV_ADJOINT, "adjoint": L.FFTMV_ADJOINT, L.FFTMV_ADJOINT: L.FFTMV_ADJOINT}
 
 
-def make_precision(prec: str = "ddddd", mode: str = "native") -> L.Precision:
-    """Precision struct from a 5-letter phase string over d/s (Section 3.2) and a GEMV mode."""
+def make_precision(prec: str = "ddddd", mode: str = "native", fft_mode: str | None = None) -> L.Precision:
+    """Precision struct from a 5-letter phase string over d/s (Section 3.2).
+
+    ``mode`` is how an FP64 block matvec computes ("native" FP64 FMA or
+    "f64x2f32" double-float); ``fft_mode`` the same for FP64 FFT/IFFT phases
+    (defaults to ``mode``).
+    """
     if len(prec) != 5 or any(c not in "ds" for c in prec):
         raise ValueError(f"precision must be 5 letters over d/s, got {prec!r}")
-    if mode not in _MODES:
-        raise ValueError(f"mode must be one of {sorted(_MODES)}")
+    fft_mode = mode if fft_mode is None else fft_mode
+    if mode not in _MODES or fft_mode not in _MODES:
+        raise ValueError(f"modes must be among {sorted(_MODES)}")
     v = [_PHASE_LETTERS[c] for c in prec]
-    return L.Precision(*v, _MODES[mode])
+    return L.Precision(*v, _MODES[mode], _MODES[fft_mode])
 
 
 def _torch():
@@ -126,16 +132,16 @@ class Operator:
         return info
 
     # -- precision ------------------------------------------------------------
-    def set_precision(self, which, prec: str = "ddddd", mode: str = "native") -> None:
-        p = make_precision(prec, mode)
+    def set_precision(self, which, prec: str = "ddddd", mode: str = "native", fft_mode: str | None = None) -> None:
+        p = make_precision(prec, mode, fft_mode)
         L.check(L.lib().fftmv_set_precision(self.handle, _WHICH[which], ctypes.byref(p)))
 
-    def get_precision(self, which) -> tuple[str, str]:
+    def get_precision(self, which) -> tuple[str, str, str]:
         p = L.Precision()
         L.check(L.lib().fftmv_get_precision(self.handle, _WHICH[which], ctypes.byref(p)))
         s = "".join("d" if v == L.FFTMV_F64 else "s" for v in (p.pad, p.fft, p.gemv, p.ifft, p.unpad))
-        mode = {v: k for k, v in _MODES.items()}[p.gemv_mode]
-        return s, mode
+        inv = {v: k for k, v in _MODES.items()}
+        return s, inv[p.gemv_mode], inv[p.fft_mode]
 
     def workspace_bytes(self, which, K: int = 1) -> int:
         out = ctypes.c_size_t()
@@ -191,8 +197,8 @@ class Operator:
 
 
 # the C ABI's verbs, for callers that prefer functions
-def set_precision(op: Operator, which, prec: str = "ddddd", mode: str = "native") -> None:
-    op.set_precision(which, prec, mode)
+def set_precision(op: Operator, which, prec: str = "ddddd", mode: str = "native", fft_mode: str | None = None) -> None:
+    op.set_precision(which, prec, mode, fft_mode)
 
 
 def matvec(op: Operator, m, out=None, stream=None):

@@ -61,7 +61,7 @@ def test_null_and_dead_handles(lib):
     fake = ctypes.c_void_p(0x1234)
     assert lib.fftmv_free(fake) == -5
     assert b"not live" in lib.fftmv_last_error()
-    p = _lib.Precision(0, 0, 0, 0, 0, 0)
+    p = _lib.Precision(0, 0, 0, 0, 0, 0, 0)
     assert lib.fftmv_set_precision(fake, 0, ctypes.byref(p)) == -5
     assert lib.fftmv_matvec(fake, None, None, 1, 0, None) == -5
     assert lib.fftmv_matvec(None, None, None, 1, 0, None) == -1
@@ -74,9 +74,11 @@ def test_null_and_dead_handles(lib):
 def test_python_precision_strings():
     from paper_2508_10202_gb300 import make_precision
     p = make_precision("dssdd", "native")
-    assert (p.pad, p.fft, p.gemv, p.ifft, p.unpad, p.gemv_mode) == (0, 1, 1, 0, 0, 0)
+    assert (p.pad, p.fft, p.gemv, p.ifft, p.unpad, p.gemv_mode, p.fft_mode) == (0, 1, 1, 0, 0, 0, 0)
     p = make_precision("ddddd", "f64x2f32")
-    assert p.gemv_mode == 1
+    assert p.gemv_mode == 1 and p.fft_mode == 1
+    p = make_precision("ddddd", "native", "f64x2f32")
+    assert p.gemv_mode == 0 and p.fft_mode == 1
     with pytest.raises(ValueError):
         make_precision("dsdx")
     with pytest.raises(ValueError):

@@ -48,6 +48,8 @@ def run_both(torch, op, m, d):
 
 
 MODES64 = [("ddddd", "native"), ("ddddd", "f64x2f32")]
+# (gemv mode, fft mode) combinations of the FP64 phases
+MODE_PAIRS = [("native", "native"), ("f64x2f32", "f64x2f32"), ("native", "f64x2f32"), ("f64x2f32", "native")]
 
 
 # --- the plain FP64 workload: Nt=64, Nd=8, Nm=32, seed 0 ---------------------
@@ -72,13 +74,14 @@ SIZES = [(1, 1, 1), (2, 1, 3), (3, 2, 5), (5, 3, 7), (7, 9, 2), (8, 1, 33), (12,
 
 
 @pytest.mark.parametrize("Nt,Nd,Nm", SIZES)
-@pytest.mark.parametrize("prec,mode", MODES64 + [("dssdd", "native"), ("sssss", "native")])
-def test_sizes(torch_cuda, Nt, Nd, Nm, prec, mode):
+@pytest.mark.parametrize("prec,mode,fft_mode", [("ddddd", g, f) for g, f in MODE_PAIRS] +
+                         [("dssdd", "native", "f64x2f32"), ("sddds", "f64x2f32", "f64x2f32"), ("sssss", "native", "native")])
+def test_sizes(torch_cuda, Nt, Nd, Nm, prec, mode, fft_mode):
     torch = torch_cuda
     Fcol, m, d = make_case(Nt, Nd, Nm, K=2, seed=Nt + 7 * Nd + 13 * Nm)
     op = gpu_op(torch, Fcol)
-    op.set_precision("F", prec, mode)
-    op.set_precision("F*", prec, mode)
+    op.set_precision("F", prec, mode, fft_mode)
+    op.set_precision("F*", prec, mode, fft_mode)
     y, x = run_both(torch, op, m, d)
     tol = TOL64 if prec == "ddddd" else TOL32
     assert oracle.rel_l2(y, oracle.matvec_direct(Fcol, m)) <= tol
@@ -127,7 +130,8 @@ def test_adjoint_identity_on_gpu(torch_cuda, prec, mode):
 ALL32 = ["".join(p) for p in itertools.product("ds", repeat=5)]
 
 
-def test_all_32_phase_configs(torch_cuda, record_property):
+@pytest.mark.parametrize("fft_mode", ["native", "f64x2f32"])
+def test_all_32_phase_configs(torch_cuda, record_property, fft_mode):
     torch = torch_cuda
     Nt, Nd, Nm = 50, 6, 70
     Fcol = synth.block_column(Nt, Nd, Nm, seed=5, perturb=True)
@@ -138,8 +142,8 @@ def test_all_32_phase_configs(torch_cuda, record_property):
     op = gpu_op(torch, Fcol)
     errs = {}
     for prec in ALL32:
-        op.set_precision("F", prec)
-        op.set_precision("F*", prec)
+        op.set_precision("F", prec, "native", fft_mode)
+        op.set_precision("F*", prec, "native", fft_mode)
         y, x = run_both(torch, op, m, d)
         e, ea = oracle.rel_l2(y, ref), oracle.rel_l2(x, refa)
         em = oracle.rel_l2(oracle.matvec_mixed(Fh, m, Nt, prec), ref)
