@@ -137,6 +137,14 @@ int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out)
 
 int fftmv_get_info(const fftmv_op* op, fftmv_info* out);
 
+/* Device status word of the operator.  Kernels that wait on asynchronous
+ * copies bound every wait; if one runs out they set a bit here
+ * (FFTMV_STATUS_WAIT_TIMEOUT), stop, and leave their outputs incomplete.
+ * Reads the word after the device's pending work (synchronous); clear != 0
+ * resets it. */
+#define FFTMV_STATUS_WAIT_TIMEOUT 1u
+int fftmv_device_status(fftmv_op* op, uint32_t* flags, int clear);
+
 /* Per-phase CUDA-event timers (the paper's per-phase timings).  While
  * enabled, every call records events on its stream around its three kernel
  * groups: [0] pad+FFT, [1] block matvec, [2] IFFT+unpad.  fftmv_phase_times

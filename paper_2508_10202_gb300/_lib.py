@@ -51,6 +51,7 @@ SIGNATURES = {
     "fftmv_rmatvec": (_INT, [_P, _P, _P, _I64, _INT, _P]),
     "fftmv_workspace_bytes": (_INT, [_P, _INT, _I64, ctypes.POINTER(ctypes.c_size_t)]),
     "fftmv_get_info": (_INT, [_P, ctypes.POINTER(Info)]),
+    "fftmv_device_status": (_INT, [_P, ctypes.POINTER(ctypes.c_uint32), _INT]),
     "fftmv_set_timing": (_INT, [_P, _INT]),
     "fftmv_phase_times": (_INT, [_P, _INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "fftmv_reset_timing": (_INT, [_P]),

@@ -106,6 +106,7 @@ struct fftmv_op {
   float2* fhat32 = nullptr;   // FP32
   fftmv_precision prec[2]{};
   cudaMemPool_t pool = nullptr;
+  unsigned int* status = nullptr;  // device status word written by bounded waits
   std::mutex mu;  // timing state
   bool timing = false;
   std::vector<TimingSet> free_sets, pending;
@@ -169,6 +170,7 @@ void release(fftmv_op* op) {
   cudaFree(op->fhat64);
   cudaFree(op->fhat_df);
   cudaFree(op->fhat32);
+  cudaFree(op->status);
   if (op->pool) cudaMemPoolDestroy(op->pool);
   for (auto& s : op->free_sets)
     for (auto e : s.ev) cudaEventDestroy(e);
@@ -241,6 +243,7 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     g.K = (int)K;
     g.x_ld_b = op->Nf * c.in_ld;
     g.y_ld_b = op->Nf * c.out_ld;
+    g.status = op->status;
     e = fwd ? launch_gemv_n(c.kind, g, s) : launch_gemv_h(c.kind, g, s);
   }
   if (ev) cudaEventRecord(ev[2], s);
@@ -402,6 +405,9 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
   if ((rc = cu(cudaMalloc(&op->twdf, L * sizeof(float4)), "cudaMalloc(twiddles)"))) return rc;
   if ((rc = cu(cudaMemcpy(op->twdf, twdf.data(), L * sizeof(float4), cudaMemcpyHostToDevice), "twiddle copy"))) return rc;
 
+  if ((rc = cu(cudaMalloc(&op->status, sizeof(unsigned int)), "cudaMalloc(status)"))) return rc;
+  if ((rc = cu(cudaMemset(op->status, 0, sizeof(unsigned int)), "cudaMemset(status)"))) return rc;
+
   const size_t fh_elems = (size_t)Nf * Nd * ldn;
   if ((rc = cu(cudaMalloc(&op->fhat64, fh_elems * sizeof(double2)), "cudaMalloc(F-hat)"))) return rc;
 
@@ -531,6 +537,18 @@ int fftmv_get_info(const fftmv_op* op, fftmv_info* out) {
   out->device = op->device;
   const size_t n = (size_t)op->Nf * op->Nd * op->ldn;
   out->fhat_bytes = n * sizeof(double2) + (op->fhat_df ? n * sizeof(float4) : 0) + (op->fhat32 ? n * sizeof(float2) : 0);
+  return FFTMV_OK;
+}
+
+int fftmv_device_status(fftmv_op* op, uint32_t* flags, int clear) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (!flags) return fail(FFTMV_EINVAL, "null output");
+  DeviceGuard dg(op->device);
+  unsigned int v = 0;
+  CUDA_TRY(cudaMemcpy(&v, op->status, sizeof v, cudaMemcpyDeviceToHost));
+  if (clear) CUDA_TRY(cudaMemset(op->status, 0, sizeof v));
+  *flags = v;
   return FFTMV_OK;
 }
 

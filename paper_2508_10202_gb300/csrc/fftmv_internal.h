@@ -85,6 +85,7 @@ struct GemvDesc {
   void* y;
   int Nf, Nd, ldn, K;
   int64_t x_ld_b, y_ld_b;  // complex-element strides between right-hand sides
+  unsigned int* status;    // device status word (bits: pipe.cuh kStatus*)
 };
 
 cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, int prec, cudaStream_t s);

@@ -24,6 +24,7 @@
 //  GEMV_F32: FP32 F-hat (8 B per entry), FP32 FMA.
 
 #include "fftmv_internal.h"
+#include "pipe.cuh"
 
 namespace fftmv {
 namespace {
@@ -176,64 +177,111 @@ struct KindF32 {
 };
 
 // ---------------------------------------------------------------------------
-// N direction: grid (ceil(Nd / R), Nf, K), T threads, U column steps in flight
+// N direction: grid (ceil(Nd / R), Nf, K).  Warp-specialised bulk-copy pipeline:
+// warp 0 (one elected thread) streams each CW-pack segment of the R rows of
+// F-hat_w and the matching segment of m-hat_w into a ring of STAGES shared
+// memory stages with cp.async.bulk, completion counted on the stage's "full"
+// mbarrier; NCW consumer warps compute from shared memory (consumer thread tc
+// owns pack tc of every segment, so its columns are tc, tc + CW, ...) and
+// release the stage through its "empty" mbarrier.  Bytes stay in flight while
+// the consumers do their double-float arithmetic.
 // ---------------------------------------------------------------------------
-template <class Kd, int R, int T, int U>
-__global__ void __launch_bounds__(T) gemv_n_kernel(GemvDesc d) {
+template <class Kd, int R, int NCW, int STAGES>
+__global__ void __launch_bounds__(32 * (NCW + 1), 2) gemv_n_kernel(GemvDesc d) {
   using Pack = typename Kd::Pack;
   using Acc = typename Kd::Acc;
-  __shared__ Acc red[T / 32][R];
+  constexpr int NC = 32 * NCW;   // consumer threads
+  constexpr int CW = NC;         // packs per row segment
+  constexpr int STAGE = (R + 1) * CW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Pack* stage = reinterpret_cast<Pack*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(stage + STAGES * STAGE);
+  uint64_t* empty = full + STAGES;
+  Acc* red = reinterpret_cast<Acc*>(empty + STAGES);   // [NCW][R]
+
   const int w = blockIdx.y, b = blockIdx.z;
   const int r0 = blockIdx.x * R;
-  const int ldp = d.ldn / Kd::P;  // packs per row
-  const Pack* __restrict__ F = static_cast<const Pack*>(d.F) + ((int64_t)w * d.Nd + r0) * ldp;
-  const Pack* __restrict__ x =
-      static_cast<const Pack*>(d.x) + (b * d.x_ld_b + (int64_t)w * d.ldn) / Kd::P;
-  // rows past Nd (last block only) re-read row r0 and are discarded
-  const Pack* rowp[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) rowp[r] = (r0 + r < d.Nd) ? F + (int64_t)r * ldp : F;
+  const int nr = min(R, d.Nd - r0);
+  const int ldp = d.ldn / Kd::P;                        // packs per row
+  const int nseg = (ldp + CW - 1) / CW;
+  const Pack* F = static_cast<const Pack*>(d.F) + ((int64_t)w * d.Nd + r0) * ldp;
+  const Pack* x = static_cast<const Pack*>(d.x) + (b * d.x_ld_b + (int64_t)w * d.ldn) / Kd::P;
 
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCW);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (warp == 0) {  // producer
+    if (lane == 0) {
+      const uint64_t policy = l2_evict_first_policy();
+      bool ok = true;
+      int c = 0;
+      for (; c < nseg; ++c) {
+        const int s = c % STAGES;
+        if (c >= STAGES && !mbar_wait(&empty[s], ((c / STAGES) & 1) ^ 1)) {
+          ok = false;
+          break;
+        }
+        const int p0 = c * CW;
+        const uint32_t bytes = (uint32_t)min(CW, ldp - p0) * (uint32_t)sizeof(Pack);
+        mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)(nr + 1));
+        Pack* st = stage + s * STAGE;
+        for (int r = 0; r < nr; ++r) bulk_g2s_hint(st + r * CW, F + (int64_t)r * ldp + p0, bytes, &full[s], policy);
+        bulk_g2s(st + R * CW, x + p0, bytes, &full[s]);
+      }
+      // no copy may outlive the CTA: wait for the last issued stages to land
+      for (int cc = max(0, c - STAGES); cc < c; ++cc)
+        if (!mbar_wait(&full[cc % STAGES], (cc / STAGES) & 1)) ok = false;
+      if (!ok) atomicOr(d.status, kStatusWaitTimeout);
+    }
+    return;
+  }
+
+  // consumers
+  const int tc = threadIdx.x - 32;
   Acc acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = Kd::zero();
-
-  int p = threadIdx.x;
-  for (; p + (U - 1) * T < ldp; p += U * T) {
-    Pack xv[U], fv[U][R];
+  for (int c = 0; c < nseg; ++c) {
+    const int s = c % STAGES;
+    if (!mbar_wait(&full[s], (c / STAGES) & 1)) {
+      atomicOr(d.status, kStatusWaitTimeout);
+      break;
+    }
+    const Pack* st = stage + s * STAGE;
+    if (tc < ldp - c * CW) {
+      // rows r >= nr (last row block only) hold stale shared memory; their
+      // accumulators are never stored
+      const Pack xv = st[R * CW + tc];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = Kd::ldX(x + p + u * T);
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int r = 0; r < R; ++r) fv[u][r] = Kd::ldF(rowp[r] + p + u * T);
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int r = 0; r < R; ++r) Kd::mac_n(acc[r], fv[u][r], xv[u]);
+      for (int r = 0; r < R; ++r) Kd::mac_n(acc[r], st[r * CW + tc], xv);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
   }
-  for (; p < ldp; p += T) {
-    const Pack xv = Kd::ldX(x + p);
-#pragma unroll
-    for (int r = 0; r < R; ++r) Kd::mac_n(acc[r], Kd::ldF(rowp[r] + p), xv);
-  }
-  // block reduction: warp shuffles, then across warps through shared memory
+  // reduction over the consumer threads: warp shuffles, then across warps
 #pragma unroll
   for (int r = 0; r < R; ++r) {
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) acc[r] = Kd::add(acc[r], Kd::shfl_xor(acc[r], m));
   }
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int cw = warp - 1;
   if (lane == 0) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) red[warp][r] = acc[r];
+    for (int r = 0; r < R; ++r) red[cw * R + r] = acc[r];
   }
-  __syncthreads();
-  if (threadIdx.x < R && r0 + (int)threadIdx.x < d.Nd) {
-    Acc s = red[0][threadIdx.x];
+  named_bar_sync(1, NC);
+  if (tc < nr) {
+    Acc sum = red[tc];
 #pragma unroll
-    for (int q = 1; q < T / 32; ++q) s = Kd::add(s, red[q][threadIdx.x]);
-    Kd::store(d.y, b * d.y_ld_b + (int64_t)w * d.Nd + r0 + threadIdx.x, s);
+    for (int q = 1; q < NCW; ++q) sum = Kd::add(sum, red[q * R + tc]);
+    Kd::store(d.y, b * d.y_ld_b + (int64_t)w * d.Nd + r0 + tc, sum);
   }
 }
 
@@ -311,13 +359,18 @@ __global__ void convert_f32_kernel(const double2* __restrict__ in, float2* __res
   }
 }
 
-constexpr int kNR = 8, kNT = 256, kNU = 2;   // N: rows per CTA, threads, column steps
+constexpr int kNR = 8, kNW = 8, kNS = 3;     // N: rows per CTA, consumer warps, pipeline stages
 constexpr int kHV = 2, kHT = 256, kHU = 4;   // H: packs per thread, threads, rows in flight
 
 template <class Kd>
 cudaError_t run_n(const GemvDesc& d, cudaStream_t s) {
+  auto kernel = gemv_n_kernel<Kd, kNR, kNW, kNS>;
+  const size_t smem = (size_t)kNS * (kNR + 1) * (32 * kNW) * sizeof(typename Kd::Pack) + 2 * kNS * sizeof(uint64_t) +
+                      (size_t)kNW * kNR * sizeof(typename Kd::Acc);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((d.Nd + kNR - 1) / kNR, d.Nf, d.K);
-  gemv_n_kernel<Kd, kNR, kNT, kNU><<<grid, kNT, 0, s>>>(d);
+  kernel<<<grid, 32 * (kNW + 1), smem, s>>>(d);
   return cudaGetLastError();
 }
 

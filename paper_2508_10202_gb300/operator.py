@@ -181,6 +181,12 @@ class Operator:
         """m = F* d (Section 2.4): d is (Nt, Nd) or (K, Nt, Nd); returns (.., Nt, Nm)."""
         return self._apply(L.FFTMV_ADJOINT, d, out, stream)
 
+    def device_status(self, clear: bool = False) -> int:
+        """Bits raised by device-side bounded waits (0 when every wait completed)."""
+        v = ctypes.c_uint32()
+        L.check(L.lib().fftmv_device_status(self.handle, ctypes.byref(v), int(bool(clear))))
+        return v.value
+
     # -- per-phase timers -----------------------------------------------------
     def set_timing(self, enable: bool = True) -> None:
         L.check(L.lib().fftmv_set_timing(self.handle, int(bool(enable))))

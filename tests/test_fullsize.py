@@ -62,6 +62,7 @@ def test_fullsize_sampled_and_adjoint(full, pf, pa, mode, tol):
     lhs, rhs = np.vdot(y, d), np.vdot(m, x)
     assert abs(lhs - rhs) <= max(tol, 1e-12) * np.linalg.norm(y) * np.linalg.norm(d)
     assert np.all(np.isfinite(y)) and np.all(np.isfinite(x))
+    assert op.device_status() == 0
 
 
 def test_fullsize_host_io_matches_device_io(full):

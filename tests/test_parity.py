@@ -86,6 +86,7 @@ def test_sizes(torch_cuda, Nt, Nd, Nm, prec, mode, fft_mode):
     tol = TOL64 if prec == "ddddd" else TOL32
     assert oracle.rel_l2(y, oracle.matvec_direct(Fcol, m)) <= tol
     assert oracle.rel_l2(x, oracle.rmatvec_direct(Fcol, d)) <= tol
+    assert op.device_status() == 0      # no bounded wait ran out
     op.free()
 
 
