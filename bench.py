@@ -294,6 +294,71 @@ def time_variant(torch, op, mt, dt, yt, xt, stream, pf, pa, steps: int) -> dict:
             "phase_ms_F": [v / nf for v in tf], "phase_ms_Fstar": [v / na for v in ta]}
 
 
+def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, K: int = 64, steps: int = 10) -> dict:
+    """K right-hand sides through F at once (FP32 phases, block matvec on the
+    tensor cores with bf16 hi/lo F-hat), the multi-RHS workload."""
+    import numpy as np
+
+    import synth
+    Nt, Nd, Nm = Fcol.shape
+    m = synth.vectors(synth.TAG_M, Nt, Nm, k=K, seed=7, dtype=np.float32)
+    mt = torch.from_numpy(m).to(dev)
+    yt = torch.empty((K, Nt, Nd), dtype=torch.float32, device=dev)
+    op.set_precision("F", "sssss", "bf16x2")
+    for _ in range(2):
+        op.matvec(mt, out=yt, stream=stream)
+    torch.cuda.synchronize()
+    op.reset_timing()
+    op.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        op.matvec(mt, out=yt, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    op.set_timing(False)
+    ms = e0.elapsed_time(e1) / steps
+    ph, n = op.phase_times("F")
+    ph = [v / n for v in ph]
+    y = yt.cpu().numpy()
+    rng = np.random.default_rng(5)
+    got, ref = [], []
+    for b in rng.choice(K, size=min(K, 6), replace=False):
+        idx = [(int(rng.integers(Nt)), int(rng.integers(Nd))) for _ in range(6)]
+        ref += list(oracle_entries(Fcol, m[b].astype(np.float64), idx))
+        got += [float(y[b, i, r]) for i, r in idx]
+    got, ref = np.array(got), np.array(ref)
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    Nf, ldn = Nt + 1, (Nm + 7) // 8 * 8
+    a_bytes = Nf * 4 * Nd * ldn * 2                    # bf16 hi/lo planes of F-hat
+    b_bytes = Nf * 2 * 2 * K * ldn * 2                 # bf16 hi/lo [Re M | Im M]
+    tc_s = ph[1] * 1e-3
+    flops_exec = 6 * 2 * 128 * (2 * K) * ldn * Nf * ((Nd + 127) // 128)
+    hbm, _ = peaks
+    bf16_peak = load_tensor_peak()
+    return {"K": K, "prec": "sssss/bf16x2 (tcgen05, bf16 hi+lo, FP32 accumulate)", "ms_call": ms,
+            "matvec_s": K / (ms * 1e-3), "phase_ms": ph, "rel_err_sampled": err,
+            "tc_kernel": {"hbm_bytes": a_bytes + b_bytes, "achieved_GBs": (a_bytes + b_bytes) / tc_s / 1e9,
+                          "hbm_frac": (a_bytes + b_bytes) / tc_s / 1e9 / hbm,
+                          "tensor_TFLOPs_executed": flops_exec / tc_s / 1e12,
+                          "tensor_frac": flops_exec / tc_s / 1e12 / bf16_peak,
+                          "useful_TFLOPs": 8.0 * Nf * Nd * Nm * K / tc_s / 1e12},
+            "algorithmic_bytes_per_call": int((Nt + 1) * Nd * Nm * 8 + K * Nt * Nm * 4 + K * Nt * Nd * 4)}
+
+
+def oracle_entries(Fcol, m, idx):
+    import oracle
+    return oracle.matvec_entries(Fcol, m, idx)
+
+
+def load_tensor_peak() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def main(args) -> None:
     import numpy as np
     import torch
@@ -410,6 +475,10 @@ def main(args) -> None:
                       "gemv_frac_Fstar": abv / (r["gemv_ms_Fstar"] * 1e-3) / 1e9 / peak})
             variants[name] = r
 
+    multi = None
+    if rank == 0 and not args.no_variants:
+        multi = bench_multi_rhs(torch, op, Fcol, dev, stream, (peak, peak_kind))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(Fcol, m, d)
@@ -426,6 +495,7 @@ def main(args) -> None:
             "gpu_launches": KERNELS_PER_MATVEC * 2 * args.steps,
             "rel_err": {"F": err_f, "Fstar": err_a, "how": "24 sampled outputs vs the oracle's definition"},
             "roofline": roofline, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "variants": variants,
+            "multi_rhs": multi,
             "setup_s": t_setup, "gen_s": t_gen,
         }
         print(json.dumps(line), flush=True)

@@ -69,8 +69,13 @@ typedef enum { FFTMV_F64 = 0, FFTMV_F32 = 1 } fftmv_phase_prec;
  *   F64X2F32 : gemv=F64 only.  F-hat as FP32 hi+lo pairs (16 B/entry, about
  *              48 significant bits), double-float arithmetic on the FP32
  *              pipe.  Not native FP64: an FP64-class emulation for GPUs whose
- *              FP64 rate cannot keep pace with memory (GB300). */
-typedef enum { FFTMV_GEMV_NATIVE = 0, FFTMV_GEMV_F64X2F32 = 1 } fftmv_gemv_mode;
+ *              FP64 rate cannot keep pace with memory (GB300).
+ *   BF16X2   : gemv=F32 only, F (FFTMV_FORWARD) only.  Many right-hand sides
+ *              on the tensor cores (tcgen05): F-hat and the transformed inputs
+ *              split into bfloat16 hi + lo parts (about 16 significant bits),
+ *              hi*hi + hi*lo + lo*hi accumulated in FP32.  Pays off once K is
+ *              large (tens of right-hand sides); its error is at FP32 level. */
+typedef enum { FFTMV_GEMV_NATIVE = 0, FFTMV_GEMV_F64X2F32 = 1, FFTMV_GEMV_BF16X2 = 2 } fftmv_gemv_mode;
 
 /* Per-phase precisions, in the execution order of the operation they are set
  * for (for F*: pad and FFT act on d, IFFT and unpad on the output m). */

@@ -25,6 +25,8 @@
 //            adds are the normwise-accurate ("sloppy") double-word sums, which
 //            is the accuracy an FFT's normwise error analysis needs.
 
+#include <cuda_bf16.h>
+
 #include <type_traits>
 
 #include "fftmv_internal.h"
@@ -376,6 +378,24 @@ __device__ __forceinline__ typename Ar<P>::C load_cx(const void* X, int64_t i, i
   }
 }
 
+// one M-hat entry (right-hand side b, frequency w, channel n) into the
+// tensor-core B operand: bf16 hi/lo of Re at row ch*N + q, of Im at row ch*N + KC + q
+template <typename P>
+__device__ __forceinline__ void store_tc(const FwdDesc& d, int b, int w, int n, typename Ar<P>::R re,
+                                         typename Ar<P>::R im) {
+  using A = Ar<P>;
+  const int ch = b / d.tc_KC, q = b - ch * d.tc_KC;
+  const int64_t plane = (int64_t)d.tc_J * d.X_ld_w;
+  __nv_bfloat16* B = static_cast<__nv_bfloat16*>(d.X) + (int64_t)w * 2 * plane + n;
+  const int64_t jr = (int64_t)(ch * d.tc_N + q) * d.X_ld_w, ji = jr + (int64_t)d.tc_KC * d.X_ld_w;
+  const float r = A::to_f(re), m = A::to_f(im);
+  const __nv_bfloat16 rh = __float2bfloat16(r), mh = __float2bfloat16(m);
+  B[jr] = rh;
+  B[plane + jr] = __float2bfloat16(r - __bfloat162float(rh));
+  B[ji] = mh;
+  B[plane + ji] = __float2bfloat16(m - __bfloat162float(mh));
+}
+
 // Forward: pad + real FFT of channel pairs; grid (pairs, K).
 template <typename Tin, typename P>
 __global__ void __launch_bounds__(256) rfft_fwd_kernel(FwdDesc d) {
@@ -397,8 +417,14 @@ __global__ void __launch_bounds__(256) rfft_fwd_kernel(FwdDesc d) {
   const bool has_a = ca < d.cols, has_b = cb < d.cols;
   const bool write_b = cb < d.out_cols;
 
+  const bool tc = d.fmt == FMT_TC;
   if (!has_a) {  // a pair of padding columns: exact zeros
     for (int w = threadIdx.x; w < Nf; w += blockDim.x) {
+      if (tc) {
+        store_tc<P>(d, b, w, ca, A::zero(), A::zero());
+        if (write_b) store_tc<P>(d, b, w, cb, A::zero(), A::zero());
+        continue;
+      }
       store_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.fmt, A::zero(), A::zero());
       if (write_b) store_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, A::zero(), A::zero());
     }
@@ -422,16 +448,15 @@ __global__ void __launch_bounds__(256) rfft_fwd_kernel(FwdDesc d) {
     const C zc = Z[w == 0 ? 0 : L - w];
     const R ar = A::half(A::add(A::re(z), A::re(zc)));
     const R ai = A::half(A::sub(A::im(z), A::im(zc)));
-    store_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.fmt, ar, ai);
-    if (write_b) {
-      if (has_b) {
-        const R br = A::half(A::add(A::im(z), A::im(zc)));
-        const R bi = A::half(A::sub(A::re(zc), A::re(z)));
-        store_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, br, bi);
-      } else {
-        store_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, A::zero(), A::zero());
-      }
+    const R br = has_b ? A::half(A::add(A::im(z), A::im(zc))) : A::zero();
+    const R bi = has_b ? A::half(A::sub(A::re(zc), A::re(z))) : A::zero();
+    if (tc) {
+      store_tc<P>(d, b, w, ca, ar, ai);
+      if (write_b) store_tc<P>(d, b, w, cb, br, bi);
+      continue;
     }
+    store_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.fmt, ar, ai);
+    if (write_b) store_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, br, bi);
   }
 }
 

@@ -104,6 +104,7 @@ struct fftmv_op {
   double2* fhat64 = nullptr;  // master F-hat [Nf][Nd][ldn], FP64
   float4* fhat_df = nullptr;  // FP32 hi/lo pairs
   float2* fhat32 = nullptr;   // FP32
+  void* fhat_bf16 = nullptr;  // bf16 planes [Nf][Re hi, Re lo, Im hi, Im lo][Nd][ldn] (tensor cores)
   fftmv_precision prec[2]{};
   cudaMemPool_t pool = nullptr;
   unsigned int* status = nullptr;  // device status word written by bounded waits
@@ -139,16 +140,19 @@ int check_prec(const fftmv_precision* p) {
   const int32_t v[5] = {p->pad, p->fft, p->gemv, p->ifft, p->unpad};
   for (int i = 0; i < 5; ++i)
     if (v[i] != FFTMV_F64 && v[i] != FFTMV_F32) return fail(FFTMV_EINVAL, "phase %d precision %d is not F64/F32", i, v[i]);
-  if (p->gemv_mode != FFTMV_GEMV_NATIVE && p->gemv_mode != FFTMV_GEMV_F64X2F32)
+  if (p->gemv_mode != FFTMV_GEMV_NATIVE && p->gemv_mode != FFTMV_GEMV_F64X2F32 && p->gemv_mode != FFTMV_GEMV_BF16X2)
     return fail(FFTMV_EINVAL, "gemv_mode %d unknown", p->gemv_mode);
   if (p->gemv_mode == FFTMV_GEMV_F64X2F32 && p->gemv != FFTMV_F64)
     return fail(FFTMV_EINVAL, "gemv_mode F64X2F32 needs an FP64 GEMV phase");
+  if (p->gemv_mode == FFTMV_GEMV_BF16X2 && p->gemv != FFTMV_F32)
+    return fail(FFTMV_EINVAL, "gemv_mode BF16X2 accumulates in FP32: it needs an FP32 GEMV phase");
   if (p->fft_mode != FFTMV_GEMV_NATIVE && p->fft_mode != FFTMV_GEMV_F64X2F32)
     return fail(FFTMV_EINVAL, "fft_mode %d unknown", p->fft_mode);
   return FFTMV_OK;
 }
 
 int gemv_kind(const fftmv_precision& p) {
+  if (p.gemv_mode == FFTMV_GEMV_BF16X2) return GEMV_TC;
   if (p.gemv == FFTMV_F32) return GEMV_F32;
   return p.gemv_mode == FFTMV_GEMV_F64X2F32 ? GEMV_DF : GEMV_F64;
 }
@@ -160,6 +164,7 @@ int fft_prec(int32_t phase, int32_t mode) {
 }
 
 const void* fhat_for(const fftmv_op* op, int kind) {
+  if (kind == GEMV_TC) return op->fhat_bf16;
   return kind == GEMV_F64 ? (const void*)op->fhat64 : kind == GEMV_DF ? (const void*)op->fhat_df : (const void*)op->fhat32;
 }
 
@@ -170,6 +175,7 @@ void release(fftmv_op* op) {
   cudaFree(op->fhat64);
   cudaFree(op->fhat_df);
   cudaFree(op->fhat32);
+  cudaFree(op->fhat_bf16);
   cudaFree(op->status);
   if (op->pool) cudaMemPoolDestroy(op->pool);
   for (auto& s : op->free_sets)
@@ -198,7 +204,12 @@ CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
   c.Cout = fwd ? op->Nd : op->Nm;
   c.in_ld = fwd ? op->ldn : op->Nd;
   c.out_ld = fwd ? op->Nd : op->ldn;
-  c.in_hat = align256((size_t)K * op->Nf * c.in_ld * fmt_bytes(c.in_fmt));
+  if (c.kind == GEMV_TC) {  // B operand planes [Nf][2][J][ldn] bf16
+    const TcShape t = tc_shape((int)K);
+    c.in_hat = align256((size_t)op->Nf * 2 * t.J * op->ldn * 2);
+  } else {
+    c.in_hat = align256((size_t)K * op->Nf * c.in_ld * fmt_bytes(c.in_fmt));
+  }
   c.out_hat = align256((size_t)K * op->Nf * c.out_ld * fmt_bytes(c.out_fmt));
   return c;
 }
@@ -230,7 +241,17 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   f.X_ld_b = op->Nf * c.in_ld;
   f.fmt = c.in_fmt;
   f.pad_single = p.pad == FFTMV_F32;
-  cudaError_t e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fprec, s);
+  cudaError_t e = cudaSuccess;
+  if (c.kind == GEMV_TC) {
+    const TcShape t = tc_shape((int)K);
+    f.tc_KC = t.KC;
+    f.tc_N = t.N;
+    f.tc_J = t.J;
+    f.X_ld_w = op->ldn;   // row length of a B plane
+    // rows no right-hand side fills (chunk padding, a short last chunk) must read as zero
+    if (2 * t.KC < t.N || (int)K % t.KC != 0) e = cudaMemsetAsync(in_hat, 0, c.in_hat, s);
+  }
+  if (e == cudaSuccess) e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fprec, s);
   if (ev) cudaEventRecord(ev[1], s);
   if (e == cudaSuccess) {
     GemvDesc g{};
@@ -244,7 +265,21 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     g.x_ld_b = op->Nf * c.in_ld;
     g.y_ld_b = op->Nf * c.out_ld;
     g.status = op->status;
-    e = fwd ? launch_gemv_n(c.kind, g, s) : launch_gemv_h(c.kind, g, s);
+    if (c.kind == GEMV_TC) {
+      TcDesc t{};
+      t.A = op->fhat_bf16;
+      t.B = in_hat;
+      t.y = out_hat;
+      t.Nf = (int)op->Nf;
+      t.Nd = (int)op->Nd;
+      t.ldn = (int)op->ldn;
+      t.K = (int)K;
+      t.y_ld_b = op->Nf * c.out_ld;
+      t.status = op->status;
+      e = launch_tc_gemm_n(t, s);
+    } else {
+      e = fwd ? launch_gemv_n(c.kind, g, s) : launch_gemv_h(c.kind, g, s);
+    }
   }
   if (ev) cudaEventRecord(ev[2], s);
   if (e == cudaSuccess) {
@@ -481,6 +516,8 @@ int fftmv_set_precision(fftmv_op* op, int which, const fftmv_precision* prec) {
   if (rc) return rc;
   if (which != FFTMV_FORWARD && which != FFTMV_ADJOINT) return fail(FFTMV_EINVAL, "which=%d is not F/F*", which);
   if ((rc = check_prec(prec))) return rc;
+  if (prec->gemv_mode == FFTMV_GEMV_BF16X2 && which != FFTMV_FORWARD)
+    return fail(FFTMV_EUNSUPPORTED, "gemv_mode BF16X2 (tensor cores) is built for F only");
   DeviceGuard dg(op->device);
   const int kind = gemv_kind(*prec);
   const size_t n = (size_t)op->Nf * op->Nd * op->ldn;
@@ -491,6 +528,10 @@ int fftmv_set_precision(fftmv_op* op, int which, const fftmv_precision* prec) {
   } else if (kind == GEMV_F32 && !op->fhat32) {
     CUDA_TRY(cudaMalloc(&op->fhat32, n * sizeof(float2)));
     CUDA_TRY(launch_convert_fhat(kind, op->fhat64, op->fhat32, n, 0));
+    CUDA_TRY(cudaStreamSynchronize(0));
+  } else if (kind == GEMV_TC && !op->fhat_bf16) {
+    CUDA_TRY(cudaMalloc(&op->fhat_bf16, n * 4 * 2));
+    CUDA_TRY(launch_convert_bf16x2(op->fhat64, op->fhat_bf16, (int)op->Nf, (int)op->Nd, (int)op->ldn, 0));
     CUDA_TRY(cudaStreamSynchronize(0));
   }
   op->prec[which] = *prec;
@@ -536,7 +577,8 @@ int fftmv_get_info(const fftmv_op* op, fftmv_info* out) {
   out->ldn = op->ldn;
   out->device = op->device;
   const size_t n = (size_t)op->Nf * op->Nd * op->ldn;
-  out->fhat_bytes = n * sizeof(double2) + (op->fhat_df ? n * sizeof(float4) : 0) + (op->fhat32 ? n * sizeof(float2) : 0);
+  out->fhat_bytes = n * sizeof(double2) + (op->fhat_df ? n * sizeof(float4) : 0) + (op->fhat32 ? n * sizeof(float2) : 0) +
+                    (op->fhat_bf16 ? n * 8 : 0);
   return FFTMV_OK;
 }
 

@@ -13,6 +13,7 @@ enum CFmt : int {
   FMT_C128 = 0,  // double2 (re, im)
   FMT_C64 = 1,   // float2 (re, im)
   FMT_DF = 2,    // float4 (re_hi, im_hi, re_lo, im_lo): value = hi + lo, |lo| <= ulp(hi)/2
+  FMT_TC = 3,    // tensor-core B operand: bf16 planes [Nf][hi, lo][J][ldn], see TcShape
 };
 
 // Arithmetic used by the per-frequency block matvec (phase 3).
@@ -20,6 +21,7 @@ enum GemvKind : int {
   GEMV_F64 = 0,   // FP64 F-hat, FP64 FMA
   GEMV_DF = 1,    // FP64-class: F-hat as FP32 hi/lo pairs, double-float arithmetic on the FP32 pipe
   GEMV_F32 = 2,   // FP32 F-hat, FP32 FMA
+  GEMV_TC = 3,    // tensor cores: bf16 hi/lo F-hat and M-hat, FP32 accumulate (forward only)
 };
 
 // Arithmetic of an FFT phase.
@@ -55,6 +57,7 @@ struct FwdDesc {
   int64_t X_ld_w, X_ld_row, X_ld_b;     // complex-element strides of X
   int fmt;                 // CFmt of X
   int pad_single;          // round the loaded input to FP32 (pad phase in FP32)
+  int tc_KC, tc_N, tc_J;   // FMT_TC only: right-hand sides per chunk, MMA N, rows per plane
 };
 
 // Inverse real FFT of Hermitian half spectra followed by unpad (phases 4-5 fused).
@@ -87,6 +90,26 @@ struct GemvDesc {
   int64_t x_ld_b, y_ld_b;  // complex-element strides between right-hand sides
   unsigned int* status;    // device status word (bits: pipe.cuh kStatus*)
 };
+
+// Tensor-core multi-RHS shape: right-hand sides go in chunks of KC <= 64;
+// chunk c's B rows are [Re M (KC rows) | Im M (KC rows) | zero padding] = N rows
+// (N = 2 KC rounded up to 16), so a plane has J = nch * N rows.
+struct TcShape {
+  int KC, N, nch, J;
+};
+TcShape tc_shape(int K);
+
+struct TcDesc {
+  const void* A;           // bf16 planes [Nf][4][Nd][ldn] (Re hi, Re lo, Im hi, Im lo)
+  const void* B;           // bf16 planes [Nf][2][J][ldn]
+  void* y;                 // FMT_C64 [K][Nf][Nd]
+  int Nf, Nd, ldn, K;
+  int64_t y_ld_b;
+  unsigned int* status;
+};
+cudaError_t launch_tc_gemm_n(const TcDesc& d, cudaStream_t s);
+cudaError_t launch_convert_bf16x2(const double2* master, void* out, int Nf, int Nd, int ldn, cudaStream_t s);
+size_t tc_smem_bytes(int N);
 
 cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, int prec, cudaStream_t s);
 cudaError_t launch_irfft_inv(const InvDesc& d, int prec, bool out_f32, cudaStream_t s);

@@ -390,8 +390,21 @@ cudaError_t run_h(const GemvDesc& d, cudaStream_t s) {
 
 }  // namespace
 
-int gemv_in_fmt(int kind) { return kind == GEMV_F64 ? FMT_C128 : kind == GEMV_DF ? FMT_DF : FMT_C64; }
-int gemv_out_fmt(int kind) { return kind == GEMV_F32 ? FMT_C64 : kind == GEMV_DF ? FMT_DF : FMT_C128; }
+int gemv_in_fmt(int kind) {
+  switch (kind) {
+    case GEMV_F64: return FMT_C128;
+    case GEMV_DF: return FMT_DF;
+    case GEMV_TC: return FMT_TC;
+    default: return FMT_C64;
+  }
+}
+int gemv_out_fmt(int kind) {
+  switch (kind) {
+    case GEMV_F64: return FMT_C128;
+    case GEMV_DF: return FMT_DF;
+    default: return FMT_C64;  // GEMV_F32 and GEMV_TC write float2
+  }
+}
 size_t fmt_bytes(int fmt) { return fmt == FMT_C64 ? 8 : 16; }
 
 cudaError_t launch_gemv_n(int kind, const GemvDesc& d, cudaStream_t s) {

@@ -1,0 +1,340 @@
+// Multi-right-hand-side block matvec on the 5th-generation tensor cores
+// (tcgen05), for the forward operator F: for every frequency w,
+//     D-hat_w (Nd x K) = F-hat_w (Nd x Nm) * M-hat_w (Nm x K)      (complex)
+// the per-frequency product of Section 2.4 phase 3 applied to K right-hand
+// sides at once, which turns the batched GEMV into a dense contraction.
+//
+// Precision: F-hat and M-hat are each split into bfloat16 hi + lo parts
+// (x = hi + lo + O(2^-18 |x|)); the three products hi*hi + hi*lo + lo*hi
+// accumulate in FP32 in tensor memory (the lo*lo term is below 2^-16 of the
+// result).
+//
+// Complex arithmetic without duplicating data: A is four planes
+// (Re hi, Re lo, Im hi, Im lo) of F-hat_w, B is [Re M | Im M] (2*KC columns,
+// hi and lo planes).  Two accumulators: acc1 = Re(F) * B, acc2 = Im(F) * B;
+// then Re D = acc1[:, q] - acc2[:, KC + q] and Im D = acc1[:, KC + q] + acc2[:, q].
+//
+// Per CTA: one frequency w, one chunk of KC <= 64 right-hand sides and one
+// tile of 128 rows; MMA tile M = 128 (rows >= Nd are zero-filled by TMA, never
+// read from HBM),
+// N = 2*KC rounded up to 16, K-step 64 bf16 (one 128-byte swizzled row).
+// Warp roles: warp 0 issues TMA loads, warp 1 owns tensor memory and issues
+// the MMAs, warps 2-5 read the accumulators (tcgen05.ld) and write D-hat.
+// Every wait is bounded (pipe.cuh); a timeout sets the status word.
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "fftmv_internal.h"
+#include "pipe.cuh"
+
+namespace fftmv {
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_BK = 64;                  // bf16 per 128-byte swizzle row
+constexpr int TC_STAGES = 2;
+constexpr int TC_THREADS = 192;            // 6 warps
+constexpr uint32_t TC_TMEM_COLS = 512;     // two accumulators of up to 256 columns
+
+// --- tcgen05 / TMA primitives (inline PTX) ---------------------------------
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t umma_desc_sw128(const void* smem) {
+  const uint64_t addr = smem_u32(smem);
+  uint64_t d = (addr & 0x3FFFFull) >> 4;    // start address
+  d |= (uint64_t)(16 >> 4) << 16;           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                   // descriptor version (sm_100)
+  d |= (uint64_t)2 << 61;                   // layout: 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = n
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int n) {
+  return (1u << 4)                         // D format: F32
+         | (1u << 7)                       // A format: BF16
+         | (1u << 10)                      // B format: BF16
+         | ((uint32_t)(n >> 3) << 17)      // N / 8
+         | ((uint32_t)(TC_M >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+  int Nf, Nd, ldn, K, KC, N, nkb;
+  int64_t y_ld_b;           // complex elements between right-hand sides of y
+  float2* y;                // D-hat [K][Nf][Nd] (FMT_C64)
+  unsigned int* status;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_n_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned tile area (the 128-byte swizzle pattern repeats every 1024 bytes)
+  unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  const int N = a.N;
+  const uint32_t a_plane = TC_M * 128;               // bytes of one 128 x 64 bf16 tile
+  const uint32_t b_plane = (uint32_t)N * 128;
+  const uint32_t stage_bytes = 4 * a_plane + 2 * b_plane;
+  unsigned char* tiles = base;
+  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + TC_STAGES * stage_bytes);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* done = empty + TC_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int w = blockIdx.x, ch = blockIdx.y, m0 = blockIdx.z * TC_M;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    mbar_init_fence();
+    tma_prefetch_desc(&mapA);
+    tma_prefetch_desc(&mapB);
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TC_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int kb = 0;
+      for (; kb < a.nkb; ++kb) {
+        const int s = kb % TC_STAGES;
+        if (kb >= TC_STAGES && !mbar_wait(&empty[s], ((kb / TC_STAGES) & 1) ^ 1)) {
+          ok = false;
+          break;
+        }
+        unsigned char* st = tiles + s * stage_bytes;
+        mbar_arrive_expect_tx(&full[s], stage_bytes);
+        for (int p = 0; p < 4; ++p) tma_load_4d(st + p * a_plane, &mapA, kb * TC_BK, m0, p, w, &full[s]);
+        for (int p = 0; p < 2; ++p) tma_load_4d(st + 4 * a_plane + p * b_plane, &mapB, kb * TC_BK, ch * N, p, w, &full[s]);
+      }
+      for (int kk = max(0, kb - TC_STAGES); kk < kb; ++kk)
+        if (!mbar_wait(&full[kk % TC_STAGES], (kk / TC_STAGES) & 1)) ok = false;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = umma_idesc_bf16(N);
+      const uint32_t acc1 = tmem, acc2 = tmem + 256;
+      int kb = 0;
+      for (; kb < a.nkb; ++kb) {
+        const int s = kb % TC_STAGES;
+        if (!mbar_wait(&full[s], (kb / TC_STAGES) & 1)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        unsigned char* st = tiles + s * stage_bytes;
+#pragma unroll
+        for (int ks = 0; ks < TC_BK / 16; ++ks) {
+          // +32 bytes per 16 bf16 along K inside the swizzled row: +2 in the address field
+          const uint64_t frh = umma_desc_sw128(st + 0 * a_plane) + 2 * ks;
+          const uint64_t frl = umma_desc_sw128(st + 1 * a_plane) + 2 * ks;
+          const uint64_t fih = umma_desc_sw128(st + 2 * a_plane) + 2 * ks;
+          const uint64_t fil = umma_desc_sw128(st + 3 * a_plane) + 2 * ks;
+          const uint64_t bh = umma_desc_sw128(st + 4 * a_plane) + 2 * ks;
+          const uint64_t bl = umma_desc_sw128(st + 4 * a_plane + b_plane) + 2 * ks;
+          const uint32_t first = (kb | ks) != 0;
+          umma_bf16(acc1, frh, bh, idesc, first);
+          umma_bf16(acc1, frh, bl, idesc, 1);
+          umma_bf16(acc1, frl, bh, idesc, 1);
+          umma_bf16(acc2, fih, bh, idesc, first);
+          umma_bf16(acc2, fih, bl, idesc, 1);
+          umma_bf16(acc2, fil, bh, idesc, 1);
+        }
+        umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+      }
+      umma_commit(done);         // accumulators complete
+    }
+  } else {  // epilogue: warps 2..5 cover TMEM lanes 32*(warp%4) .. +31
+    const int row = m0 + 32 * (warp % 4) + lane;
+    if (!mbar_wait(done, 0)) ok = false;
+    tc_fence_after();
+    if (__all_sync(0xffffffffu, ok)) {  // tcgen05.ld is warp-collective
+      const uint32_t lane_addr = (uint32_t)(32 * (warp % 4)) << 16;
+      const int KC = a.KC;
+      for (int q0 = 0; q0 < KC; q0 += 16) {
+        float a1r[16], a1i[16], a2r[16], a2i[16];
+        tmem_ld16(tmem + lane_addr + q0, a1r);             // Re F * Re M
+        tmem_ld16(tmem + lane_addr + KC + q0, a1i);        // Re F * Im M
+        tmem_ld16(tmem + 256 + lane_addr + q0, a2r);       // Im F * Re M
+        tmem_ld16(tmem + 256 + lane_addr + KC + q0, a2i);  // Im F * Im M
+        if (row < a.Nd) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int q = q0 + i;
+            const int b = ch * KC + q;
+            if (q < KC && b < a.K)
+              a.y[b * a.y_ld_b + (int64_t)w * a.Nd + row] = make_float2(a1r[i] - a2i[i], a1i[i] + a2r[i]);
+          }
+        }
+      }
+    }
+  }
+  if (!ok) atomicOr(a.status, kStatusWaitTimeout);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TC_TMEM_COLS);
+  }
+}
+
+// master FP64 F-hat [Nf][Nd][ldn] -> four bf16 planes [Nf][4][Nd][ldn]: Re hi, Re lo, Im hi, Im lo
+__global__ void convert_bf16x2_kernel(const double2* __restrict__ in, __nv_bfloat16* __restrict__ out, int Nd, int ldn,
+                                      int64_t n) {
+  const int64_t plane = (int64_t)Nd * ldn;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    const int64_t w = i / plane, rem = i - w * plane;
+    __nv_bfloat16* o = out + w * 4 * plane + rem;
+    const __nv_bfloat16 rh = __double2bfloat16(v.x), ih = __double2bfloat16(v.y);
+    o[0] = rh;
+    o[plane] = __double2bfloat16(v.x - (double)__bfloat162float(rh));
+    o[2 * plane] = ih;
+    o[3 * plane] = __double2bfloat16(v.y - (double)__bfloat162float(ih));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 4-D bf16 map {inner, rows, planes, freqs} with a box of 64 x box_rows x 1 x 1, 128-byte swizzle
+cudaError_t make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t rows, uint64_t planes,
+                     uint64_t freqs, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[4] = {inner, rows, planes, freqs};
+  const cuuint64_t strides[3] = {inner * 2, inner * rows * 2, inner * rows * planes * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)TC_BK, box_rows, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+TcShape tc_shape(int K) {
+  TcShape t{};
+  t.KC = K < 64 ? K : 64;
+  t.N = ((2 * t.KC + 15) / 16) * 16;
+  t.nch = (K + t.KC - 1) / t.KC;
+  t.J = t.nch * t.N;
+  return t;
+}
+
+size_t tc_smem_bytes(int N) {
+  const size_t stage = 4 * (size_t)TC_M * 128 + 2 * (size_t)N * 128;
+  return 1024 + TC_STAGES * stage + (2 * TC_STAGES + 1) * sizeof(uint64_t) + 16;
+}
+
+cudaError_t launch_convert_bf16x2(const double2* master, void* out, int Nf, int Nd, int ldn, cudaStream_t s) {
+  const int64_t n = (int64_t)Nf * Nd * ldn;
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t want = (n + threads - 1) / threads;
+  const int blocks = (int)(want < 152 * 32 ? want : 152 * 32);
+  convert_bf16x2_kernel<<<blocks, threads, 0, s>>>(master, static_cast<__nv_bfloat16*>(out), Nd, ldn, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm_n(const TcDesc& d, cudaStream_t s) {
+  if (d.Nf == 0 || d.K == 0) return cudaSuccess;
+  const TcShape t = tc_shape(d.K);
+  CUtensorMap mapA, mapB;
+  cudaError_t e = make_map(&mapA, d.A, (uint64_t)d.ldn, (uint64_t)d.Nd, 4, (uint64_t)d.Nf, TC_M);
+  if (e != cudaSuccess) return e;
+  e = make_map(&mapB, d.B, (uint64_t)d.ldn, (uint64_t)t.J, 2, (uint64_t)d.Nf, (uint32_t)t.N);
+  if (e != cudaSuccess) return e;
+  TcArgs a{};
+  a.Nf = d.Nf;
+  a.Nd = d.Nd;
+  a.ldn = d.ldn;
+  a.K = d.K;
+  a.KC = t.KC;
+  a.N = t.N;
+  a.nkb = (d.ldn + TC_BK - 1) / TC_BK;
+  a.y_ld_b = d.y_ld_b;
+  a.y = static_cast<float2*>(d.y);
+  a.status = d.status;
+  const size_t smem = tc_smem_bytes(t.N);
+  e = cudaFuncSetAttribute(tc_gemm_n_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(d.Nf, t.nch, (d.Nd + TC_M - 1) / TC_M);
+  tc_gemm_n_kernel<<<grid, TC_THREADS, smem, s>>>(mapA, mapB, a);
+  return cudaGetLastError();
+}
+
+}  // namespace fftmv

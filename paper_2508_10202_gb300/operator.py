@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib as L
 
 _PHASE_LETTERS = {"d": L.FFTMV_F64, "s": L.FFTMV_F32}
-_MODES = {"native": L.FFTMV_GEMV_NATIVE, "f64x2f32": L.FFTMV_GEMV_F64X2F32}
+_MODES = {"native": L.FFTMV_GEMV_NATIVE, "f64x2f32": L.FFTMV_GEMV_F64X2F32, "bf16x2": L.FFTMV_GEMV_BF16X2}
 _WHICH = {"F": L.FFTMV_FORWARD, "forward": L.FFTMV_FORWARD, L.FFTMV_FORWARD: L.FFTMV_FORWARD,
           "F*": L.FFTMV_ADJOINT, "adjoint": L.FFTMV_ADJOINT, L.FFTMV_ADJOINT: L.FFTMV_ADJOINT}
 
@@ -27,7 +27,8 @@ def make_precision(prec: str = "ddddd", mode: str = "native", fft_mode: str | No
     """
     if len(prec) != 5 or any(c not in "ds" for c in prec):
         raise ValueError(f"precision must be 5 letters over d/s, got {prec!r}")
-    fft_mode = mode if fft_mode is None else fft_mode
+    if fft_mode is None:
+        fft_mode = "f64x2f32" if mode == "f64x2f32" else "native"
     if mode not in _MODES or fft_mode not in _MODES:
         raise ValueError(f"modes must be among {sorted(_MODES)}")
     v = [_PHASE_LETTERS[c] for c in prec]
