@@ -267,21 +267,26 @@ template <typename P, bool INV> struct Dft<P, 8, INV> {
   }
 };
 
-// One Stockham pass of radix R over a length-L signal: reads `in`, writes `out`.
-// Butterfly j (< L/R) takes in[j + q L/R], applies the twiddle of its position
-// k = j mod Ns inside the current sub-transform, and writes out[(j-k) R + k + q Ns].
+// One Stockham pass of radix R over nsig length-L signals stored back to back
+// ([nsig][L]): reads `in`, writes `out`.  Butterfly j (< L/R) of a signal takes
+// in[j + q L/R], applies the twiddle of its position k = j mod Ns inside the
+// current sub-transform, and writes out[(j-k) R + k + q Ns].
 template <typename P, int R, bool INV>
 __device__ __forceinline__ void stockham_pass(const typename Ar<P>::C* __restrict__ in, typename Ar<P>::C* __restrict__ out,
-                                              int L, int Ns, const typename Ar<P>::C* __restrict__ tw) {
+                                              int L, int nsig, int Ns, const typename Ar<P>::C* __restrict__ tw) {
   using A = Ar<P>;
   using C = typename A::C;
   const int nb = L / R;
   const int tw_step = L / (Ns * R);
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+  for (int jt = threadIdx.x; jt < nsig * nb; jt += blockDim.x) {
+    const int sig = jt / nb;
+    const int j = jt - sig * nb;
     const int k = j % Ns;
+    const C* src = in + sig * L;
+    C* dst = out + sig * L;
     C v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = in[j + q * nb];
+    for (int q = 0; q < R; ++q) v[q] = src[j + q * nb];
     if (Ns > 1) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
@@ -293,13 +298,13 @@ __device__ __forceinline__ void stockham_pass(const typename Ar<P>::C* __restric
     Dft<P, R, INV>::run(v);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int q = 0; q < R; ++q) out[base + q * Ns] = v[q];
+    for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
   }
 }
 
-// Full FFT of the signal in buf0; returns the buffer that holds the result.
+// FFT of the nsig signals in buf0; returns the buffer that holds the results.
 template <typename P, bool INV>
-__device__ typename Ar<P>::C* fft_smem(typename Ar<P>::C* buf0, typename Ar<P>::C* buf1, const FftPlan& plan,
+__device__ typename Ar<P>::C* fft_smem(typename Ar<P>::C* buf0, typename Ar<P>::C* buf1, const FftPlan& plan, int nsig,
                                        const typename Ar<P>::C* __restrict__ tw) {
   using C = typename Ar<P>::C;
   C* in = buf0;
@@ -309,11 +314,11 @@ __device__ typename Ar<P>::C* fft_smem(typename Ar<P>::C* buf0, typename Ar<P>::
     const int R = plan.rad[p];
     __syncthreads();
     switch (R) {
-      case 2: stockham_pass<P, 2, INV>(in, out, plan.L, Ns, tw); break;
-      case 3: stockham_pass<P, 3, INV>(in, out, plan.L, Ns, tw); break;
-      case 4: stockham_pass<P, 4, INV>(in, out, plan.L, Ns, tw); break;
-      case 5: stockham_pass<P, 5, INV>(in, out, plan.L, Ns, tw); break;
-      default: stockham_pass<P, 8, INV>(in, out, plan.L, Ns, tw); break;
+      case 2: stockham_pass<P, 2, INV>(in, out, plan.L, nsig, Ns, tw); break;
+      case 3: stockham_pass<P, 3, INV>(in, out, plan.L, nsig, Ns, tw); break;
+      case 4: stockham_pass<P, 4, INV>(in, out, plan.L, nsig, Ns, tw); break;
+      case 5: stockham_pass<P, 5, INV>(in, out, plan.L, nsig, Ns, tw); break;
+      default: stockham_pass<P, 8, INV>(in, out, plan.L, nsig, Ns, tw); break;
     }
     Ns *= R;
     C* t = in;
@@ -396,67 +401,66 @@ __device__ __forceinline__ void store_tc(const FwdDesc& d, int b, int w, int n, 
   B[plane + ji] = __float2bfloat16(m - __bfloat162float(mh));
 }
 
-// Forward: pad + real FFT of channel pairs; grid (pairs, K).
-template <typename Tin, typename P>
+// Forward: pad + real FFT; grid (row x channel group, K).  A CTA owns NP
+// adjacent channel pairs (2 NP channels): consecutive threads take consecutive
+// channels at one time step (loads) or one frequency (stores), so every warp
+// access covers 2 NP contiguous channels.
+template <typename Tin, typename P, int NP>
 __global__ void __launch_bounds__(256) rfft_fwd_kernel(FwdDesc d) {
   using A = Ar<P>;
   using C = typename A::C;
   using R = typename A::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + d.plan.L;
   const int L = d.plan.L;
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + NP * L;
   const int Nf = L / 2 + 1;
-  const int pairs_per_row = (d.out_cols + 1) / 2;
-  const int row = blockIdx.x / pairs_per_row;
-  const int ca = 2 * (blockIdx.x % pairs_per_row);
-  const int cb = ca + 1;
+  constexpr int NCH = 2 * NP;
+  const int groups = (d.out_cols + NCH - 1) / NCH;
+  const int row = blockIdx.x / groups;
+  const int c0 = (blockIdx.x - row * groups) * NCH;
   const int b = blockIdx.y;
   const int64_t xo = b * d.x_ld_b + row * d.x_ld_row;
   const int64_t Xo = b * d.X_ld_b + row * d.X_ld_row;
-  const bool has_a = ca < d.cols, has_b = cb < d.cols;
-  const bool write_b = cb < d.out_cols;
-
   const bool tc = d.fmt == FMT_TC;
-  if (!has_a) {  // a pair of padding columns: exact zeros
-    for (int w = threadIdx.x; w < Nf; w += blockDim.x) {
-      if (tc) {
-        store_tc<P>(d, b, w, ca, A::zero(), A::zero());
-        if (write_b) store_tc<P>(d, b, w, cb, A::zero(), A::zero());
-        continue;
-      }
-      store_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.fmt, A::zero(), A::zero());
-      if (write_b) store_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, A::zero(), A::zero());
+
+  // phase 1: load (cast to the pad, then the FFT precision) and zero pad;
+  // channel pair p is the complex signal x_{c0+2p} + i x_{c0+2p+1}
+  const int nload = d.Nt * NCH;
+  for (int i = threadIdx.x; i < L * NCH; i += blockDim.x) {
+    const int t = i / NCH, cc = i - t * NCH;
+    const int c = c0 + cc;
+    R v = A::zero();
+    if (i < nload && c < d.cols) v = load_real<P, Tin>(d.x, xo + t * d.x_ld_t + c, d.pad_single);
+    C& z = buf0[(cc >> 1) * L + t];
+    if constexpr (std::is_same<P, DFP>::value) {
+      if (cc & 1) { z.y = v.h; z.w = v.l; } else { z.x = v.h; z.z = v.l; }
+    } else {
+      if (cc & 1) z.y = v; else z.x = v;
     }
-    return;
   }
-  // phase 1: load, cast to the pad precision, then to the FFT precision; zero pad
-  for (int t = threadIdx.x; t < L; t += blockDim.x) {
-    R va = A::zero(), vb = A::zero();
-    if (t < d.Nt) {
-      va = load_real<P, Tin>(d.x, xo + t * d.x_ld_t + ca, d.pad_single);
-      if (has_b) vb = load_real<P, Tin>(d.x, xo + t * d.x_ld_t + cb, d.pad_single);
-    }
-    buf0[t] = A::mk(va, vb);
-  }
-  // phase 2: complex FFT of z = x_a + i x_b
+  // phase 2: complex FFTs
   const C* tw = static_cast<const C*>(d.tw);
-  const C* Z = fft_smem<P, false>(buf0, buf1, d.plan, tw);
+  const C* Z = fft_smem<P, false>(buf0, buf1, d.plan, NP, tw);
   // split: X_a = (Z_w + conj Z_{L-w}) / 2,  X_b = (Z_w - conj Z_{L-w}) / (2i)
-  for (int w = threadIdx.x; w < Nf; w += blockDim.x) {
-    const C z = Z[w];
-    const C zc = Z[w == 0 ? 0 : L - w];
-    const R ar = A::half(A::add(A::re(z), A::re(zc)));
-    const R ai = A::half(A::sub(A::im(z), A::im(zc)));
-    const R br = has_b ? A::half(A::add(A::im(z), A::im(zc))) : A::zero();
-    const R bi = has_b ? A::half(A::sub(A::re(zc), A::re(z))) : A::zero();
-    if (tc) {
-      store_tc<P>(d, b, w, ca, ar, ai);
-      if (write_b) store_tc<P>(d, b, w, cb, br, bi);
-      continue;
+  for (int i = threadIdx.x; i < Nf * NCH; i += blockDim.x) {
+    const int w = i / NCH, cc = i - w * NCH;
+    const int c = c0 + cc;
+    if (c >= d.out_cols) continue;
+    R xr = A::zero(), xi = A::zero();
+    if (c < d.cols) {
+      const C z = Z[(cc >> 1) * L + w];
+      const C zc = Z[(cc >> 1) * L + (w == 0 ? 0 : L - w)];
+      if (cc & 1) {
+        xr = A::half(A::add(A::im(z), A::im(zc)));
+        xi = A::half(A::sub(A::re(zc), A::re(z)));
+      } else {
+        xr = A::half(A::add(A::re(z), A::re(zc)));
+        xi = A::half(A::sub(A::im(z), A::im(zc)));
+      }
     }
-    store_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.fmt, ar, ai);
-    if (write_b) store_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.fmt, br, bi);
+    if (tc) store_tc<P>(d, b, w, c, xr, xi);
+    else store_cx<P>(d.X, Xo + w * d.X_ld_w + c, d.fmt, xr, xi);
   }
 }
 
@@ -469,43 +473,48 @@ __device__ __forceinline__ void store_real(void* y, int64_t i, typename Ar<P>::R
   }
 }
 
-// Inverse: Hermitian assembly + inverse complex FFT + unpad; grid (pairs, K).
-template <typename P, typename Tout>
+// Inverse: Hermitian assembly + inverse complex FFT + unpad; grid (channel group, K).
+template <typename P, typename Tout, int NP>
 __global__ void __launch_bounds__(256) irfft_inv_kernel(InvDesc d) {
   using A = Ar<P>;
   using C = typename A::C;
   using R = typename A::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + d.plan.L;
   const int L = d.plan.L;
+  C* buf0 = reinterpret_cast<C*>(smem_raw);
+  C* buf1 = buf0 + NP * L;
   const int Nf = L / 2 + 1;
-  const int ca = 2 * blockIdx.x, cb = ca + 1;
+  constexpr int NCH = 2 * NP;
+  const int c0 = blockIdx.x * NCH;
   const int b = blockIdx.y;
-  const bool has_b = cb < d.cols;
   const int64_t Xo = b * d.X_ld_b;
-  // Z_w = X_a(w) + i X_b(w) over the full circle, X(L-w) = conj X(w);
-  // the DC and Nyquist terms of a real signal's spectrum are taken as real.
-  for (int w = threadIdx.x; w < Nf; w += blockDim.x) {
-    const C a = load_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt);
-    const C bb = has_b ? load_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : A::mk(A::zero(), A::zero());
+  // Z_w = X_a(w) + i X_b(w) over the full circle, X(L-w) = conj X(w); the DC and
+  // Nyquist terms of a real signal's spectrum are taken as real.  Thread i
+  // reads channel pair i % NP at frequency i / NP (two adjacent entries).
+  for (int i = threadIdx.x; i < Nf * NP; i += blockDim.x) {
+    const int w = i / NP, p = i - w * NP;
+    const int ca = c0 + 2 * p, cb = ca + 1;
+    const C zero = A::mk(A::zero(), A::zero());
+    const C a = ca < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt) : zero;
+    const C bb = cb < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : zero;
+    C* z = buf0 + p * L;
     if (w == 0 || w == Nf - 1) {
-      buf0[w] = A::mk(A::re(a), A::re(bb));
+      z[w] = A::mk(A::re(a), A::re(bb));
     } else {
-      buf0[w] = A::mk(A::sub(A::re(a), A::im(bb)), A::add(A::im(a), A::re(bb)));
-      buf0[L - w] = A::mk(A::add(A::re(a), A::im(bb)), A::sub(A::re(bb), A::im(a)));
+      z[w] = A::mk(A::sub(A::re(a), A::im(bb)), A::add(A::im(a), A::re(bb)));
+      z[L - w] = A::mk(A::add(A::re(a), A::im(bb)), A::sub(A::re(bb), A::im(a)));
     }
   }
   const C* tw = static_cast<const C*>(d.tw);
-  const C* z = fft_smem<P, true>(buf0, buf1, d.plan, tw);
+  const C* z = fft_smem<P, true>(buf0, buf1, d.plan, NP, tw);
   const Kc inv_L{d.inv_L, d.inv_L_hi, d.inv_L_lo};
-  for (int t = threadIdx.x; t < d.Nt; t += blockDim.x) {
-    const C zt = z[t];
-    const R va = A::mulk(A::re(zt), inv_L);
-    const R vb = A::mulk(A::im(zt), inv_L);
-    const int64_t yo = b * d.y_ld_b + t * d.y_ld_t;
-    store_real<Tout, P>(d.y, yo + ca, va, d.unpad_single);
-    if (has_b) store_real<Tout, P>(d.y, yo + cb, vb, d.unpad_single);
+  for (int i = threadIdx.x; i < d.Nt * NCH; i += blockDim.x) {
+    const int t = i / NCH, cc = i - t * NCH;
+    const int c = c0 + cc;
+    if (c >= d.cols) continue;
+    const C zt = z[(cc >> 1) * L + t];
+    const R v = A::mulk((cc & 1) ? A::im(zt) : A::re(zt), inv_L);
+    store_real<Tout, P>(d.y, b * d.y_ld_b + t * d.y_ld_t + c, v, d.unpad_single);
   }
 }
 
@@ -515,25 +524,55 @@ cudaError_t prep(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
+// channel pairs per CTA: the most (up to 8) whose two buffers fit in kFftSmemCap
+constexpr size_t kFftSmemCap = 100 * 1024;
+template <typename P>
+int pairs_per_cta(int L) {
+  const size_t per_pair = 2 * (size_t)L * sizeof(typename Ar<P>::C);
+  int np = 8;
+  while (np > 1 && np * per_pair > kFftSmemCap) np /= 2;
+  return np;
+}
+
+template <typename Tin, typename P, int NP>
+cudaError_t fwd_launch_np(const FwdDesc& d, cudaStream_t s) {
+  const int groups = (d.out_cols + 2 * NP - 1) / (2 * NP);
+  dim3 grid(d.rows * groups, d.K);
+  const size_t smem = 2 * (size_t)NP * d.plan.L * sizeof(typename Ar<P>::C);
+  cudaError_t e = prep(rfft_fwd_kernel<Tin, P, NP>, smem);
+  if (e != cudaSuccess) return e;
+  rfft_fwd_kernel<Tin, P, NP><<<grid, 256, smem, s>>>(d);
+  return cudaGetLastError();
+}
+
 template <typename Tin, typename P>
 cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
-  const int pairs = d.rows * ((d.out_cols + 1) / 2);
-  dim3 grid(pairs, d.K);
-  const size_t smem = 2 * (size_t)d.plan.L * sizeof(typename Ar<P>::C);
-  cudaError_t e = prep(rfft_fwd_kernel<Tin, P>, smem);
+  switch (pairs_per_cta<P>(d.plan.L)) {
+    case 8: return fwd_launch_np<Tin, P, 8>(d, s);
+    case 4: return fwd_launch_np<Tin, P, 4>(d, s);
+    case 2: return fwd_launch_np<Tin, P, 2>(d, s);
+    default: return fwd_launch_np<Tin, P, 1>(d, s);
+  }
+}
+
+template <typename P, typename Tout, int NP>
+cudaError_t inv_launch_np(const InvDesc& d, cudaStream_t s) {
+  dim3 grid((d.cols + 2 * NP - 1) / (2 * NP), d.K);
+  const size_t smem = 2 * (size_t)NP * d.plan.L * sizeof(typename Ar<P>::C);
+  cudaError_t e = prep(irfft_inv_kernel<P, Tout, NP>, smem);
   if (e != cudaSuccess) return e;
-  rfft_fwd_kernel<Tin, P><<<grid, 256, smem, s>>>(d);
+  irfft_inv_kernel<P, Tout, NP><<<grid, 256, smem, s>>>(d);
   return cudaGetLastError();
 }
 
 template <typename P, typename Tout>
 cudaError_t inv_launch(const InvDesc& d, cudaStream_t s) {
-  dim3 grid((d.cols + 1) / 2, d.K);
-  const size_t smem = 2 * (size_t)d.plan.L * sizeof(typename Ar<P>::C);
-  cudaError_t e = prep(irfft_inv_kernel<P, Tout>, smem);
-  if (e != cudaSuccess) return e;
-  irfft_inv_kernel<P, Tout><<<grid, 256, smem, s>>>(d);
-  return cudaGetLastError();
+  switch (pairs_per_cta<P>(d.plan.L)) {
+    case 8: return inv_launch_np<P, Tout, 8>(d, s);
+    case 4: return inv_launch_np<P, Tout, 4>(d, s);
+    case 2: return inv_launch_np<P, Tout, 2>(d, s);
+    default: return inv_launch_np<P, Tout, 1>(d, s);
+  }
 }
 
 }  // namespace

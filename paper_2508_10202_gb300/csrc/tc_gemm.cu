@@ -19,7 +19,13 @@
 // read from HBM),
 // N = 2*KC rounded up to 16, K-step 64 bf16 (one 128-byte swizzled row).
 // Warp roles: warp 0 issues TMA loads, warp 1 owns tensor memory and issues
-// the MMAs, warps 2-5 read the accumulators (tcgen05.ld) and write D-hat.
+// the MMAs, warps 2-9 drain the accumulators (tcgen05.ld) and write D-hat.
+//
+// Accumulation in groups: the tensor core's internal FP32 accumulation loses
+// accuracy over long contractions (10^4 terms here), so the MMAs accumulate
+// TC_GROUP k-blocks at a time into one of two TMEM accumulator sets; the
+// epilogue warps add each finished set into FP32 registers while the MMAs fill
+// the other set, and hand the set back through a "drained" mbarrier.
 // Every wait is bounded (pipe.cuh); a timeout sets the status word.
 
 #include <cuda.h>
@@ -35,8 +41,10 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_BK = 64;                  // bf16 per 128-byte swizzle row
 constexpr int TC_STAGES = 2;
-constexpr int TC_THREADS = 192;            // 6 warps
-constexpr uint32_t TC_TMEM_COLS = 512;     // two accumulators of up to 256 columns
+constexpr int TC_GROUP = 8;                // k-blocks accumulated in TMEM before a drain
+constexpr int TC_EPI_WARPS = 8;            // two per TMEM lane quadrant
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
+constexpr uint32_t TC_TMEM_COLS = 512;     // two accumulator sets of [acc1 | acc2], 128 columns each
 
 // --- tcgen05 / TMA primitives (inline PTX) ---------------------------------
 
@@ -133,18 +141,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   unsigned char* tiles = base;
   uint64_t* full = reinterpret_cast<uint64_t*>(tiles + TC_STAGES * stage_bytes);
   uint64_t* empty = full + TC_STAGES;
-  uint64_t* done = empty + TC_STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* ready = empty + TC_STAGES;     // [2]: accumulator set holds a finished group
+  uint64_t* drained = ready + 2;           // [2]: epilogue has read the set
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 2);
 
   const int w = blockIdx.x, ch = blockIdx.y, m0 = blockIdx.z * TC_M;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int ngroups = (a.nkb + TC_GROUP - 1) / TC_GROUP;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&ready[s], 1);
+      mbar_init(&drained[s], TC_EPI_WARPS);
+    }
     mbar_init_fence();
     tma_prefetch_desc(&mapA);
     tma_prefetch_desc(&mapB);
@@ -176,15 +189,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       const uint32_t idesc = umma_idesc_bf16(N);
-      const uint32_t acc1 = tmem, acc2 = tmem + 256;
-      int kb = 0;
-      for (; kb < a.nkb; ++kb) {
+      for (int kb = 0; kb < a.nkb && ok; ++kb) {
+        const int g = kb / TC_GROUP, set = g & 1;
+        const bool first = kb % TC_GROUP == 0;
+        // the set was last used by group g-2: wait until the epilogue has read it
+        if (first && g >= 2 && !mbar_wait(&drained[set], ((g >> 1) - 1) & 1)) {
+          ok = false;
+          break;
+        }
         const int s = kb % TC_STAGES;
         if (!mbar_wait(&full[s], (kb / TC_STAGES) & 1)) {
           ok = false;
           break;
         }
         tc_fence_after();
+        const uint32_t acc1 = tmem + 256 * set, acc2 = acc1 + 128;
         unsigned char* st = tiles + s * stage_bytes;
 #pragma unroll
         for (int ks = 0; ks < TC_BK / 16; ++ks) {
@@ -195,39 +214,65 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint64_t fil = umma_desc_sw128(st + 3 * a_plane) + 2 * ks;
           const uint64_t bh = umma_desc_sw128(st + 4 * a_plane) + 2 * ks;
           const uint64_t bl = umma_desc_sw128(st + 4 * a_plane + b_plane) + 2 * ks;
-          const uint32_t first = (kb | ks) != 0;
-          umma_bf16(acc1, frh, bh, idesc, first);
+          const uint32_t acc = !(first && ks == 0);
+          umma_bf16(acc1, frh, bh, idesc, acc);
           umma_bf16(acc1, frh, bl, idesc, 1);
           umma_bf16(acc1, frl, bh, idesc, 1);
-          umma_bf16(acc2, fih, bh, idesc, first);
+          umma_bf16(acc2, fih, bh, idesc, acc);
           umma_bf16(acc2, fih, bl, idesc, 1);
           umma_bf16(acc2, fil, bh, idesc, 1);
         }
-        umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+        umma_commit(&empty[s]);                                         // stage reusable
+        if (kb % TC_GROUP == TC_GROUP - 1 || kb == a.nkb - 1) umma_commit(&ready[set]);  // group done
       }
-      umma_commit(done);         // accumulators complete
     }
-  } else {  // epilogue: warps 2..5 cover TMEM lanes 32*(warp%4) .. +31
+  } else {  // epilogue: warps 2..9; TMEM lane quadrant warp % 4, half of the RHS columns each
+    const int ew = warp - 2;
     const int row = m0 + 32 * (warp % 4) + lane;
-    if (!mbar_wait(done, 0)) ok = false;
-    tc_fence_after();
-    if (__all_sync(0xffffffffu, ok)) {  // tcgen05.ld is warp-collective
-      const uint32_t lane_addr = (uint32_t)(32 * (warp % 4)) << 16;
-      const int KC = a.KC;
-      for (int q0 = 0; q0 < KC; q0 += 16) {
-        float a1r[16], a1i[16], a2r[16], a2i[16];
-        tmem_ld16(tmem + lane_addr + q0, a1r);             // Re F * Re M
-        tmem_ld16(tmem + lane_addr + KC + q0, a1i);        // Re F * Im M
-        tmem_ld16(tmem + 256 + lane_addr + q0, a2r);       // Im F * Re M
-        tmem_ld16(tmem + 256 + lane_addr + KC + q0, a2i);  // Im F * Im M
-        if (row < a.Nd) {
+    const uint32_t lane_addr = (uint32_t)(32 * (warp % 4)) << 16;
+    const int KC = a.KC, hw = (KC + 1) / 2;
+    const int qlo = (ew / 4) * hw, qn = min(hw, KC - qlo);   // this warp's RHS columns [qlo, qlo + qn)
+    float sre[32], sim[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) sre[i] = sim[i] = 0.f;
+    for (int g = 0; g < ngroups; ++g) {
+      const int set = g & 1;
+      bool got = mbar_wait(&ready[set], (g >> 1) & 1);
+      if (!__all_sync(0xffffffffu, got)) {  // tcgen05.ld is warp-collective
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t t1 = tmem + lane_addr + 256 * set, t2 = t1 + 128;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (c * 16 < qn) {
+          float a1r[16], a1i[16], a2r[16], a2i[16];
+          const int q0 = qlo + c * 16;
+          tmem_ld16(t1 + q0, a1r);        // Re F * Re M
+          tmem_ld16(t1 + KC + q0, a1i);   // Re F * Im M
+          tmem_ld16(t2 + q0, a2r);        // Im F * Re M
+          tmem_ld16(t2 + KC + q0, a2i);   // Im F * Im M
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int q = q0 + i;
-            const int b = ch * KC + q;
-            if (q < KC && b < a.K)
-              a.y[b * a.y_ld_b + (int64_t)w * a.Nd + row] = make_float2(a1r[i] - a2i[i], a1i[i] + a2r[i]);
+            sre[c * 16 + i] += a1r[i] - a2i[i];
+            sim[c * 16 + i] += a1i[i] + a2r[i];
           }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&drained[set]);
+    }
+    if (ok && row < a.Nd) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int q = qlo + c * 16 + i;
+          const int b = ch * KC + q;
+          if (c * 16 + i < qn && b < a.K)
+            a.y[b * a.y_ld_b + (int64_t)w * a.Nd + row] = make_float2(sre[c * 16 + i], sim[c * 16 + i]);
         }
       }
     }
@@ -297,7 +342,7 @@ TcShape tc_shape(int K) {
 
 size_t tc_smem_bytes(int N) {
   const size_t stage = 4 * (size_t)TC_M * 128 + 2 * (size_t)N * 128;
-  return 1024 + TC_STAGES * stage + (2 * TC_STAGES + 1) * sizeof(uint64_t) + 16;
+  return 1024 + TC_STAGES * stage + (2 * TC_STAGES + 4) * sizeof(uint64_t) + 16;
 }
 
 cudaError_t launch_convert_bf16x2(const double2* master, void* out, int Nf, int Nd, int ldn, cudaStream_t s) {
