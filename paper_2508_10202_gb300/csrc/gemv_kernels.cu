@@ -286,19 +286,28 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 2) gemv_n_kernel(GemvDesc d) {
 }
 
 // ---------------------------------------------------------------------------
-// H direction: grid (ceil(ldp / (T V)), Nf, K); d-hat_w in shared memory
+// H direction: grid (ceil(ldp / (T V)), Nf, ceil(K / KB)).  d-hat_w of KB
+// right-hand sides sits in shared memory; every F-hat pack loaded from HBM
+// serves all KB of them, so K right-hand sides cost ceil(K / KB) passes over
+// F-hat instead of K.
 // ---------------------------------------------------------------------------
-template <class Kd, int V, int T, int U>
+template <class Kd, int V, int T, int U, int KB>
 __global__ void __launch_bounds__(T) gemv_h_kernel(GemvDesc d) {
   using Pack = typename Kd::Pack;
   using Elem = typename Kd::Elem;
   using Acc = typename Kd::Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Elem* xs = reinterpret_cast<Elem*>(smem_raw);
-  const int w = blockIdx.y, b = blockIdx.z;
+  Elem* xs = reinterpret_cast<Elem*>(smem_raw);   // [KB][Nd]
+  const int w = blockIdx.y;
+  const int b0 = blockIdx.z * KB;
+  const int nb = min(KB, d.K - b0);
   const int ldp = d.ldn / Kd::P;
-  const Elem* __restrict__ x = static_cast<const Elem*>(d.x) + b * d.x_ld_b + (int64_t)w * d.Nd;
-  for (int r = threadIdx.x; r < d.Nd; r += T) xs[r] = x[r];
+  for (int i = threadIdx.x; i < KB * d.Nd; i += T) {
+    const int kb = i / d.Nd, r = i - kb * d.Nd;
+    const Elem* __restrict__ x = static_cast<const Elem*>(d.x) + (b0 + kb) * d.x_ld_b + (int64_t)w * d.Nd;
+    if (kb < nb) xs[i] = x[r];
+    else xs[i] = Elem{};  // right-hand sides past K: zeros, results not stored
+  }
   __syncthreads();
 
   const Pack* __restrict__ F = static_cast<const Pack*>(d.F) + (int64_t)w * d.Nd * ldp;
@@ -308,11 +317,13 @@ __global__ void __launch_bounds__(T) gemv_h_kernel(GemvDesc d) {
     const int p = blockIdx.x * (T * V) + v * T + threadIdx.x;
     pc[v] = p < ldp ? p : ldp - 1;  // out-of-range columns re-read the last one; not stored
   }
-  Acc acc[V][Kd::P];
+  Acc acc[KB][V][Kd::P];
 #pragma unroll
-  for (int v = 0; v < V; ++v)
+  for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
-    for (int e = 0; e < Kd::P; ++e) acc[v][e] = Kd::zero();
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int e = 0; e < Kd::P; ++e) acc[kb][v][e] = Kd::zero();
 
   int r = 0;
   for (; r + U <= d.Nd; r += U) {
@@ -323,23 +334,36 @@ __global__ void __launch_bounds__(T) gemv_h_kernel(GemvDesc d) {
       for (int v = 0; v < V; ++v) fv[u][v] = Kd::ldF(F + (int64_t)(r + u) * ldp + pc[v]);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const Elem xr = xs[r + u];
 #pragma unroll
-      for (int v = 0; v < V; ++v) Kd::mac_h(acc[v], fv[u][v], xr);
+      for (int kb = 0; kb < KB; ++kb) {
+        const Elem xr = xs[kb * d.Nd + r + u];
+#pragma unroll
+        for (int v = 0; v < V; ++v) Kd::mac_h(acc[kb][v], fv[u][v], xr);
+      }
     }
   }
   for (; r < d.Nd; ++r) {
-    const Elem xr = xs[r];
+    Pack fv[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) Kd::mac_h(acc[v], Kd::ldF(F + (int64_t)r * ldp + pc[v]), xr);
+    for (int v = 0; v < V; ++v) fv[v] = Kd::ldF(F + (int64_t)r * ldp + pc[v]);
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) {
+      const Elem xr = xs[kb * d.Nd + r];
+#pragma unroll
+      for (int v = 0; v < V; ++v) Kd::mac_h(acc[kb][v], fv[v], xr);
+    }
   }
-  const int64_t yo = b * d.y_ld_b + (int64_t)w * d.ldn;
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const int p = blockIdx.x * (T * V) + v * T + threadIdx.x;
-    if (p < ldp) {
+  for (int kb = 0; kb < KB; ++kb) {
+    if (kb >= nb) break;
+    const int64_t yo = (b0 + kb) * d.y_ld_b + (int64_t)w * d.ldn;
 #pragma unroll
-      for (int e = 0; e < Kd::P; ++e) Kd::store(d.y, yo + (int64_t)p * Kd::P + e, acc[v][e]);
+    for (int v = 0; v < V; ++v) {
+      const int p = blockIdx.x * (T * V) + v * T + threadIdx.x;
+      if (p < ldp) {
+#pragma unroll
+        for (int e = 0; e < Kd::P; ++e) Kd::store(d.y, yo + (int64_t)p * Kd::P + e, acc[kb][v][e]);
+      }
     }
   }
 }
@@ -374,18 +398,28 @@ cudaError_t run_n(const GemvDesc& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <class Kd>
-cudaError_t run_h(const GemvDesc& d, cudaStream_t s) {
+template <class Kd, int KB>
+cudaError_t run_h_kb(const GemvDesc& d, cudaStream_t s) {
   const int ldp = d.ldn / Kd::P;
-  dim3 grid((ldp + kHT * kHV - 1) / (kHT * kHV), d.Nf, d.K);
-  const size_t smem = (size_t)d.Nd * sizeof(typename Kd::Elem);
+  dim3 grid((ldp + kHT * kHV - 1) / (kHT * kHV), d.Nf, (d.K + KB - 1) / KB);
+  const size_t smem = (size_t)KB * d.Nd * sizeof(typename Kd::Elem);
+  auto kernel = gemv_h_kernel<Kd, kHV, kHT, kHU, KB>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gemv_h_kernel<Kd, kHV, kHT, kHU>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  gemv_h_kernel<Kd, kHV, kHT, kHU><<<grid, kHT, smem, s>>>(d);
+  kernel<<<grid, kHT, smem, s>>>(d);
   return cudaGetLastError();
+}
+
+// right-hand sides per CTA: up to 8 for FP32 (8-byte entries), 4 otherwise
+template <class Kd>
+cudaError_t run_h(const GemvDesc& d, cudaStream_t s) {
+  const int kmax = Kd::P == 2 ? 8 : 4;
+  if (d.K >= 8 && kmax >= 8) return run_h_kb<Kd, 8>(d, s);
+  if (d.K >= 4) return run_h_kb<Kd, 4>(d, s);
+  if (d.K >= 2) return run_h_kb<Kd, 2>(d, s);
+  return run_h_kb<Kd, 1>(d, s);
 }
 
 }  // namespace
