@@ -65,6 +65,7 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
     p.add_argument("--Nt", type=int, default=NT)
     p.add_argument("--Nd", type=int, default=ND)
     p.add_argument("--Nm", type=int, default=NM)
@@ -346,6 +347,72 @@ def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, K: int = 64, steps: int
             "algorithmic_bytes_per_call": int((Nt + 1) * Nd * Nm * 8 + K * Nt * Nm * 4 + K * Nt * Nd * 4)}
 
 
+# the served mix: four resident operators (Nt, Nd, Nm), blocks N(0,1) in float32
+SERVE_OPS = {"op128": (128, 16, 1000), "op256": (256, 64, 4000), "op500": (500, 100, 10000),
+             "op1000": (1000, 200, 8000)}
+SERVE_BUDGET = 150 * 10**9
+
+
+def bench_serving(torch, dev, n_cap: int = 120, n_load: int = 160, seed: int = 0) -> dict:
+    """Poisson arrivals of F / F* requests (50/50, K ~ U{1..64}, operator uniform),
+    admitted by a 150 GB HBM budget; capacity from a saturated run, then p50/p99
+    at 0.5x and 0.9x of it."""
+    import numpy as np
+
+    import synth
+    from paper_2508_10202_gb300 import Operator
+    from paper_2508_10202_gb300.serve import Request, Server, latency_stats
+    t0 = time.perf_counter()
+    ops = {}
+    for i, (name, shp) in enumerate(SERVE_OPS.items()):
+        col = synth.block_column(*shp, seed=100 + i, dtype=np.float32).astype(np.float64)
+        ops[name] = Operator(col)
+        del col
+    setup_s = time.perf_counter() - t0
+    srv = Server(ops, budget_bytes=SERVE_BUDGET, n_streams=4)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    pools = {}
+    for name, op in ops.items():
+        pools[(name, "F")] = torch.randn((64, op.Nt, op.Nm), generator=gen, device=dev)
+        pools[(name, "F*")] = torch.randn((64, op.Nt, op.Nd), generator=gen, device=dev)
+    rng = np.random.default_rng(seed)
+    names = list(ops)
+
+    def requests(n):
+        out = []
+        for _ in range(n):
+            name = names[rng.integers(len(names))]
+            which = "F" if rng.random() < 0.5 else "F*"
+            K = int(rng.integers(1, 65))
+            out.append(Request(name, which, pools[(name, which)][:K]))
+        return out
+
+    for r in requests(48):              # warm-up: capture the graphs
+        srv.submit(r)
+    srv.run_until_idle()
+    cap_reqs = requests(n_cap)          # capacity: everything arrives at once
+    out = srv.run_schedule([(0.0, r) for r in cap_reqs])
+    cap = latency_stats(out)
+    mean_k = 32.5
+    res = {"operators": {k: list(v) for k, v in SERVE_OPS.items()}, "budget_bytes": SERVE_BUDGET,
+           "resident_bytes": srv.resident, "setup_s": setup_s, "precision": srv.precision,
+           "capacity": cap}
+    for frac in (0.5, 0.9):
+        lam = frac * cap["matvec_s"] / mean_k          # requests per second
+        reqs = requests(n_load)
+        t = np.cumsum(rng.exponential(1.0 / lam, size=n_load))
+        st = latency_stats(srv.run_schedule(list(zip(t, reqs))))
+        st["offered_req_s"] = lam
+        res[f"load_{frac}"] = st
+    res["batches"] = srv.n_batches
+    res["graph_batches"] = srv.n_graph_batches
+    srv.close()
+    for op in ops.values():
+        op.free()
+    return res
+
+
 def oracle_entries(Fcol, m, idx):
     import oracle
     return oracle.matvec_entries(Fcol, m, idx)
@@ -483,6 +550,13 @@ def main(args) -> None:
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(Fcol, m, d)
 
+    served = None
+    if rank == 0 and not args.no_serve:
+        op.free()                       # make room for the served operators
+        del mt, dt, yt, xt
+        torch.cuda.empty_cache()
+        served = bench_serving(torch, dev)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -495,11 +569,14 @@ def main(args) -> None:
             "gpu_launches": KERNELS_PER_MATVEC * 2 * args.steps,
             "rel_err": {"F": err_f, "Fstar": err_a, "how": "24 sampled outputs vs the oracle's definition"},
             "roofline": roofline, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "variants": variants,
-            "multi_rhs": multi,
+            "multi_rhs": multi, "served": served,
+            "served_p50_ms": served["load_0.9"]["p50_ms"] if served else None,
+            "served_p99_ms": served["load_0.9"]["p99_ms"] if served else None,
             "setup_s": t_setup, "gen_s": t_gen,
         }
         print(json.dumps(line), flush=True)
-    op.free()
+    if served is None:
+        op.free()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -140,6 +140,17 @@ int fftmv_rmatvec(fftmv_op* op, const void* d, void* m, int64_t K, int io_dtype,
  * (which = FORWARD or ADJOINT), not counting host-I/O staging. */
 int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out);
 
+/* F m (which = FFTMV_FORWARD) or F* d (FFTMV_ADJOINT) with caller-supplied
+ * scratch, so a serving layer can own and account for every byte and capture
+ * the call in a CUDA graph (no allocation happens inside).
+ *   in, out   : device pointers (host buffers: FFTMV_EINVAL).
+ *   workspace : device memory, 256-byte aligned, at least
+ *               fftmv_workspace_bytes(op, which, K) bytes; used only by this
+ *               call until the stream has run it.
+ * Everything else as fftmv_matvec / fftmv_rmatvec. */
+int fftmv_apply_ws(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io_dtype, void* workspace,
+                   size_t workspace_bytes, void* stream);
+
 int fftmv_get_info(const fftmv_op* op, fftmv_info* out);
 
 /* Device status word of the operator.  Kernels that wait on asynchronous

@@ -565,6 +565,36 @@ int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out)
   return FFTMV_OK;
 }
 
+int fftmv_apply_ws(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io, void* workspace,
+                   size_t workspace_bytes, void* stream) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (which != FFTMV_FORWARD && which != FFTMV_ADJOINT) return fail(FFTMV_EINVAL, "which=%d is not F/F*", which);
+  if (K < 0) return fail(FFTMV_EINVAL, "K = %lld < 0", (long long)K);
+  if (io != FFTMV_IO_F64 && io != FFTMV_IO_F32) return fail(FFTMV_EINVAL, "io_dtype %d unknown", io);
+  if (K == 0) return FFTMV_OK;
+  if (!in || !out || !workspace) return fail(FFTMV_EINVAL, "null input, output or workspace");
+  if (K > 65535) return fail(FFTMV_EUNSUPPORTED, "K = %lld exceeds 65535 right-hand sides per call", (long long)K);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(FFTMV_EINVAL, "workspace is not 256-byte aligned");
+  DeviceGuard dg(op->device);
+  const CallPlan c = plan_call(op, which, K);
+  if (workspace_bytes < c.in_hat + c.out_hat)
+    return fail(FFTMV_EINVAL, "workspace of %zu bytes; this call needs %zu", workspace_bytes, c.in_hat + c.out_hat);
+  const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
+  const size_t in_bytes = (size_t)K * op->Nt * c.Cin * esz;
+  const size_t out_bytes = (size_t)K * op->Nt * c.Cout * esz;
+  {
+    const char* a = static_cast<const char*>(in);
+    const char* b = static_cast<const char*>(out);
+    if (a < b + out_bytes && b < a + in_bytes) return fail(FFTMV_EINVAL, "input and output overlap");
+  }
+  if (!is_device_ptr(in) || !is_device_ptr(out)) return fail(FFTMV_EINVAL, "fftmv_apply_ws takes device pointers only");
+  char* ws = static_cast<char*>(workspace);
+  cudaError_t e = launch_phases(op, which, c, in, out, ws, ws + c.in_hat, K, io, static_cast<cudaStream_t>(stream), nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "matvec kernels");
+  return FFTMV_OK;
+}
+
 int fftmv_get_info(const fftmv_op* op, fftmv_info* out) {
   int rc = check_op(op);
   if (rc) return rc;

@@ -174,6 +174,17 @@ class Operator:
         L.check(fn(self.handle, ptr, optr, K, io, _stream_handle(stream, dev)))
         return out
 
+    def apply_ws(self, which, x, out, workspace, stream=None):
+        """F x or F* x into ``out`` with caller-owned scratch (a device uint8 tensor of at
+        least workspace_bytes(which, K) bytes, 256-byte aligned); device tensors only."""
+        w = _WHICH[which]
+        ptr, io, shape, is_cuda, dev = _array_info(x)
+        optr, oio, _, _, _ = _array_info(out)
+        K = 1 if len(shape) == 2 else shape[0]
+        L.check(L.lib().fftmv_apply_ws(self.handle, w, ptr, optr, K, io, workspace.data_ptr(),
+                                       workspace.numel() * workspace.element_size(), _stream_handle(stream, dev)))
+        return out
+
     def matvec(self, m, out=None, stream=None):
         """d = F m (Section 2.4): m is (Nt, Nm) or (K, Nt, Nm); returns (.., Nt, Nd)."""
         return self._apply(L.FFTMV_FORWARD, m, out, stream)
