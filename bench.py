@@ -413,6 +413,22 @@ def bench_serving(torch, dev, n_cap: int = 120, n_load: int = 160, seed: int = 0
     return res
 
 
+def bench_pareto(torch, op, mt, dt, yt, xt, stream) -> dict:
+    """All 32 per-phase configurations (x the FP64 modes) for F and F*, timed and
+    compared with the all-FP64 output; the Pareto front and the fastest
+    configuration under the paper's 1e-7 tolerance and under 1e-5 / 1e-12."""
+    from paper_2508_10202_gb300.pareto import best_under, pareto_front, sweep
+    res = {}
+    for which, x, out in (("F", mt, yt), ("F*", dt, xt)):
+        op.set_precision(which, "ddddd", "native", "native")
+        ref = (op.matvec(x, stream=stream) if which == "F" else op.rmatvec(x, stream=stream)).clone()
+        pts = sweep(op, which, x, ref, reps=5, stream=stream)
+        res[which] = {"n_configs": len(pts), "front": pareto_front(pts),
+                      "best_1e-7": best_under(pts, 1e-7), "best_1e-5": best_under(pts, 1e-5),
+                      "best_1e-12": best_under(pts, 1e-12)}
+    return res
+
+
 def oracle_entries(Fcol, m, idx):
     import oracle
     return oracle.matvec_entries(Fcol, m, idx)
@@ -542,6 +558,10 @@ def main(args) -> None:
                       "gemv_frac_Fstar": abv / (r["gemv_ms_Fstar"] * 1e-3) / 1e9 / peak})
             variants[name] = r
 
+    pareto = None
+    if rank == 0 and not args.no_variants:
+        pareto = bench_pareto(torch, op, mt, dt, yt, xt, stream)
+
     multi = None
     if rank == 0 and not args.no_variants:
         multi = bench_multi_rhs(torch, op, Fcol, dev, stream, (peak, peak_kind))
@@ -569,7 +589,7 @@ def main(args) -> None:
             "gpu_launches": KERNELS_PER_MATVEC * 2 * args.steps,
             "rel_err": {"F": err_f, "Fstar": err_a, "how": "24 sampled outputs vs the oracle's definition"},
             "roofline": roofline, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "variants": variants,
-            "multi_rhs": multi, "served": served,
+            "multi_rhs": multi, "pareto": pareto, "served": served,
             "served_p50_ms": served["load_0.9"]["p50_ms"] if served else None,
             "served_p99_ms": served["load_0.9"]["p99_ms"] if served else None,
             "setup_s": t_setup, "gen_s": t_gen,

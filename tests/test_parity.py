@@ -258,3 +258,33 @@ def test_adjoint_many_rhs(torch_cuda, prec, mode, K):
         xb = op.rmatvec(torch.from_numpy(d[b]).cuda()).cpu().numpy()
         np.testing.assert_array_equal(xb, x[b])
     op.free()
+
+
+@pytest.mark.parametrize("pr,pc", [(1, 3), (2, 2)])
+def test_shard_simulation_on_one_gpu(torch_cuda, pr, pc):
+    # the p_r x p_c partition on one GPU: one operator per block, partial results
+    # summed on the device (the phase-5 reductions) equal the full operator
+    torch = torch_cuda
+    from paper_2508_10202_gb300.distributed import local_block, shard_bounds
+    Nt, Nd, Nm = 50, 13, 301
+    Fcol, m, d = make_case(Nt, Nd, Nm, seed=21)
+    full = gpu_op(torch, Fcol)
+    full.set_precision("F", "ddddd", "f64x2f32")
+    full.set_precision("F*", "ddddd", "f64x2f32")
+    y_full, x_full = run_both(torch, full, m[0], d[0])
+    y = torch.zeros((Nt, Nd), dtype=torch.float64, device="cuda")
+    x = torch.zeros((Nt, Nm), dtype=torch.float64, device="cuda")
+    for rank in range(pr * pc):
+        i, j = divmod(rank, pc)
+        r0, r1 = shard_bounds(Nd, pr, i)
+        c0, c1 = shard_bounds(Nm, pc, j)
+        blk = gpu_op(torch, np.ascontiguousarray(local_block(Fcol, rank, pr, pc)))
+        blk.set_precision("F", "ddddd", "f64x2f32")
+        blk.set_precision("F*", "ddddd", "f64x2f32")
+        y[:, r0:r1] += blk.matvec(torch.from_numpy(np.ascontiguousarray(m[0][:, c0:c1])).cuda())
+        x[:, c0:c1] += blk.rmatvec(torch.from_numpy(np.ascontiguousarray(d[0][:, r0:r1])).cuda())
+        blk.free()
+    assert oracle.rel_l2(y.cpu().numpy(), y_full) <= 1e-12
+    assert oracle.rel_l2(x.cpu().numpy(), x_full) <= 1e-12
+    assert oracle.rel_l2(y.cpu().numpy(), oracle.matvec_direct(Fcol, m[0])) <= 1e-12
+    full.free()
