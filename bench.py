@@ -55,6 +55,8 @@ VARIANTS = {
     "all_fp32": (("sssss", "native", "native"), ("sssss", "native", "native")),
 }
 KERNELS_PER_MATVEC = 3
+# mean DRAM bytes per launch of gemv_n/gemv_h<KindDF> at the paper shape
+GEMV_DF_TRAFFIC = 16.15e9
 
 
 def parse_args(argv=None):
@@ -66,6 +68,7 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-multi", action="store_true")
     p.add_argument("--Nt", type=int, default=NT)
     p.add_argument("--Nd", type=int, default=ND)
     p.add_argument("--Nm", type=int, default=NM)
@@ -519,8 +522,11 @@ def main(args) -> None:
     ab = algorithmic_bytes(Nt, Nd, Nm, fhat_entry_bytes(*HEADLINE))
     gemv_ms = (tf[1] + ta[1]) / (nf + na)
     achieved = ab / (gemv_ms * 1e-3) / 1e9
+    # DRAM bytes per launch of the same two kernels from ncu --set full at Nm=1000,
+    # scaled x10 to the full operator (profiles/gemv_df_Nm1000_full.md)
+    traffic = GEMV_DF_TRAFFIC if (Nt, Nd, Nm) == (NT, ND, NM) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "gemv_n_kernel<KindDF> (F) / gemv_h_kernel<KindDF> (F*)",
+                "traffic": traffic, "kernel": "gemv_n_kernel<KindDF> (F) / gemv_h_kernel<KindDF> (F*)",
                 "bytes_per_launch": ab, "gemv_ms_F": tf[1] / nf, "gemv_ms_Fstar": ta[1] / na,
                 "frac_F": ab / (tf[1] / nf * 1e-3) / 1e9 / peak, "frac_Fstar": ab / (ta[1] / na * 1e-3) / 1e9 / peak,
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
@@ -563,7 +569,7 @@ def main(args) -> None:
         pareto = bench_pareto(torch, op, mt, dt, yt, xt, stream)
 
     multi = None
-    if rank == 0 and not args.no_variants:
+    if rank == 0 and not args.no_multi:
         multi = bench_multi_rhs(torch, op, Fcol, dev, stream, (peak, peak_kind))
 
     cpu = None

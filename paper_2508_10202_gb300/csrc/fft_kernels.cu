@@ -383,30 +383,12 @@ __device__ __forceinline__ typename Ar<P>::C load_cx(const void* X, int64_t i, i
   }
 }
 
-// one M-hat entry (right-hand side b, frequency w, channel n) into the
-// tensor-core B operand: bf16 hi/lo of Re at row ch*N + q, of Im at row ch*N + KC + q
-template <typename P>
-__device__ __forceinline__ void store_tc(const FwdDesc& d, int b, int w, int n, typename Ar<P>::R re,
-                                         typename Ar<P>::R im) {
-  using A = Ar<P>;
-  const int ch = b / d.tc_KC, q = b - ch * d.tc_KC;
-  const int64_t plane = (int64_t)d.tc_J * d.X_ld_w;
-  __nv_bfloat16* B = static_cast<__nv_bfloat16*>(d.X) + (int64_t)w * 2 * plane + n;
-  const int64_t jr = (int64_t)(ch * d.tc_N + q) * d.X_ld_w, ji = jr + (int64_t)d.tc_KC * d.X_ld_w;
-  const float r = A::to_f(re), m = A::to_f(im);
-  const __nv_bfloat16 rh = __float2bfloat16(r), mh = __float2bfloat16(m);
-  B[jr] = rh;
-  B[plane + jr] = __float2bfloat16(r - __bfloat162float(rh));
-  B[ji] = mh;
-  B[plane + ji] = __float2bfloat16(m - __bfloat162float(mh));
-}
-
 // Forward: pad + real FFT; grid (row x channel group, K).  A CTA owns NP
 // adjacent channel pairs (2 NP channels): consecutive threads take consecutive
 // channels at one time step (loads) or one frequency (stores), so every warp
 // access covers 2 NP contiguous channels.
 template <typename Tin, typename P, int NP>
-__global__ void __launch_bounds__(256) rfft_fwd_kernel(FwdDesc d) {
+__global__ void __launch_bounds__(256, 3) rfft_fwd_kernel(FwdDesc d) {
   using A = Ar<P>;
   using C = typename A::C;
   using R = typename A::R;
@@ -426,25 +408,41 @@ __global__ void __launch_bounds__(256) rfft_fwd_kernel(FwdDesc d) {
 
   // phase 1: load (cast to the pad, then the FFT precision) and zero pad;
   // channel pair p is the complex signal x_{c0+2p} + i x_{c0+2p+1}
+  // (8 loads in flight per thread before the shared-memory writes: the loop is
+  // latency bound otherwise)
+  constexpr int U = 8;
   const int nload = d.Nt * NCH;
-  for (int i = threadIdx.x; i < L * NCH; i += blockDim.x) {
-    const int t = i / NCH, cc = i - t * NCH;
-    const int c = c0 + cc;
-    R v = A::zero();
-    if (i < nload && c < d.cols) v = load_real<P, Tin>(d.x, xo + t * d.x_ld_t + c, d.pad_single);
-    C& z = buf0[(cc >> 1) * L + t];
-    if constexpr (std::is_same<P, DFP>::value) {
-      if (cc & 1) { z.y = v.h; z.w = v.l; } else { z.x = v.h; z.z = v.l; }
-    } else {
-      if (cc & 1) z.y = v; else z.x = v;
+  for (int i0 = threadIdx.x; i0 < L * NCH; i0 += U * blockDim.x) {
+    R v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      const int t = i / NCH, c = c0 + (i - t * NCH);
+      v[u] = (i < nload && c < d.cols) ? load_real<P, Tin>(d.x, xo + t * d.x_ld_t + c, d.pad_single) : A::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i >= L * NCH) break;
+      const int t = i / NCH, cc = i - t * NCH;
+      C& z = buf0[(cc >> 1) * L + t];
+      if constexpr (std::is_same<P, DFP>::value) {
+        if (cc & 1) { z.y = v[u].h; z.w = v[u].l; } else { z.x = v[u].h; z.z = v[u].l; }
+      } else {
+        if (cc & 1) z.y = v[u]; else z.x = v[u];
+      }
     }
   }
   // phase 2: complex FFTs
   const C* tw = static_cast<const C*>(d.tw);
   const C* Z = fft_smem<P, false>(buf0, buf1, d.plan, NP, tw);
-  // split: X_a = (Z_w + conj Z_{L-w}) / 2,  X_b = (Z_w - conj Z_{L-w}) / (2i)
+  // split: X_a = (Z_w + conj Z_{L-w}) / 2,  X_b = (Z_w - conj Z_{L-w}) / (2i).
+  // Spectra for the tensor cores go channel-major, T[b][c][w] (FMT_TC, float2),
+  // with consecutive threads on consecutive frequencies; the others go
+  // frequency-major with consecutive threads on consecutive channels.
   for (int i = threadIdx.x; i < Nf * NCH; i += blockDim.x) {
-    const int w = i / NCH, cc = i - w * NCH;
+    const int w = tc ? i % Nf : i / NCH;
+    const int cc = tc ? i / Nf : i - w * NCH;
     const int c = c0 + cc;
     if (c >= d.out_cols) continue;
     R xr = A::zero(), xi = A::zero();
@@ -459,7 +457,7 @@ __global__ void __launch_bounds__(256) rfft_fwd_kernel(FwdDesc d) {
         xi = A::half(A::sub(A::im(z), A::im(zc)));
       }
     }
-    if (tc) store_tc<P>(d, b, w, c, xr, xi);
+    if (tc) static_cast<float2*>(d.X)[((int64_t)b * d.out_cols + c) * Nf + w] = make_float2(A::to_f(xr), A::to_f(xi));
     else store_cx<P>(d.X, Xo + w * d.X_ld_w + c, d.fmt, xr, xi);
   }
 }
@@ -475,7 +473,7 @@ __device__ __forceinline__ void store_real(void* y, int64_t i, typename Ar<P>::R
 
 // Inverse: Hermitian assembly + inverse complex FFT + unpad; grid (channel group, K).
 template <typename P, typename Tout, int NP>
-__global__ void __launch_bounds__(256) irfft_inv_kernel(InvDesc d) {
+__global__ void __launch_bounds__(256, 3) irfft_inv_kernel(InvDesc d) {
   using A = Ar<P>;
   using C = typename A::C;
   using R = typename A::R;
@@ -491,18 +489,31 @@ __global__ void __launch_bounds__(256) irfft_inv_kernel(InvDesc d) {
   // Z_w = X_a(w) + i X_b(w) over the full circle, X(L-w) = conj X(w); the DC and
   // Nyquist terms of a real signal's spectrum are taken as real.  Thread i
   // reads channel pair i % NP at frequency i / NP (two adjacent entries).
-  for (int i = threadIdx.x; i < Nf * NP; i += blockDim.x) {
-    const int w = i / NP, p = i - w * NP;
-    const int ca = c0 + 2 * p, cb = ca + 1;
-    const C zero = A::mk(A::zero(), A::zero());
-    const C a = ca < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt) : zero;
-    const C bb = cb < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : zero;
-    C* z = buf0 + p * L;
-    if (w == 0 || w == Nf - 1) {
-      z[w] = A::mk(A::re(a), A::re(bb));
-    } else {
-      z[w] = A::mk(A::sub(A::re(a), A::im(bb)), A::add(A::im(a), A::re(bb)));
-      z[L - w] = A::mk(A::add(A::re(a), A::im(bb)), A::sub(A::re(bb), A::im(a)));
+  constexpr int U = 4;   // loads in flight per thread
+  const C zero = A::mk(A::zero(), A::zero());
+  for (int i0 = threadIdx.x; i0 < Nf * NP; i0 += U * blockDim.x) {
+    C a[U], bb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      const int w = i / NP, p = i - w * NP;
+      const int ca = c0 + 2 * p, cb = ca + 1;
+      const bool in = i < Nf * NP;
+      a[u] = in && ca < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt) : zero;
+      bb[u] = in && cb < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i >= Nf * NP) break;
+      const int w = i / NP, p = i - w * NP;
+      C* z = buf0 + p * L;
+      if (w == 0 || w == Nf - 1) {
+        z[w] = A::mk(A::re(a[u]), A::re(bb[u]));
+      } else {
+        z[w] = A::mk(A::sub(A::re(a[u]), A::im(bb[u])), A::add(A::im(a[u]), A::re(bb[u])));
+        z[L - w] = A::mk(A::add(A::re(a[u]), A::im(bb[u])), A::sub(A::re(bb[u]), A::im(a[u])));
+      }
     }
   }
   const C* tw = static_cast<const C*>(d.tw);

@@ -204,9 +204,9 @@ CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
   c.Cout = fwd ? op->Nd : op->Nm;
   c.in_ld = fwd ? op->ldn : op->Nd;
   c.out_ld = fwd ? op->Nd : op->ldn;
-  if (c.kind == GEMV_TC) {  // B operand planes [Nf][2][J][ldn] bf16
-    const TcShape t = tc_shape((int)K);
-    c.in_hat = align256((size_t)op->Nf * 2 * t.J * op->ldn * 2);
+  if (c.kind == GEMV_TC) {  // B operand planes [Nf][2][J][ldn] bf16, then the channel-major spectra
+    c.in_hat = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)op->ldn)) +
+               align256(tc_spectrum_bytes((int)K, (int)op->Nf, (int)op->ldn));
   } else {
     c.in_hat = align256((size_t)K * op->Nf * c.in_ld * fmt_bytes(c.in_fmt));
   }
@@ -242,16 +242,17 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   f.fmt = c.in_fmt;
   f.pad_single = p.pad == FFTMV_F32;
   cudaError_t e = cudaSuccess;
+  void* tc_T = nullptr;
   if (c.kind == GEMV_TC) {
     const TcShape t = tc_shape((int)K);
-    f.tc_KC = t.KC;
-    f.tc_N = t.N;
-    f.tc_J = t.J;
-    f.X_ld_w = op->ldn;   // row length of a B plane
-    // rows no right-hand side fills (chunk padding, a short last chunk) must read as zero
-    if (2 * t.KC < t.N || (int)K % t.KC != 0) e = cudaMemsetAsync(in_hat, 0, c.in_hat, s);
+    const size_t bbytes = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)op->ldn));
+    tc_T = static_cast<char*>(in_hat) + bbytes;
+    f.X = tc_T;
+    // B rows no right-hand side fills (chunk padding, a short last chunk) must read as zero
+    if (2 * t.KC < t.N || (int)K % t.KC != 0) e = cudaMemsetAsync(in_hat, 0, bbytes, s);
   }
   if (e == cudaSuccess) e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fprec, s);
+  if (e == cudaSuccess && tc_T) e = launch_tc_pack(tc_T, in_hat, (int)K, (int)op->Nf, (int)op->ldn, s);
   if (ev) cudaEventRecord(ev[1], s);
   if (e == cudaSuccess) {
     GemvDesc g{};

@@ -13,7 +13,8 @@ enum CFmt : int {
   FMT_C128 = 0,  // double2 (re, im)
   FMT_C64 = 1,   // float2 (re, im)
   FMT_DF = 2,    // float4 (re_hi, im_hi, re_lo, im_lo): value = hi + lo, |lo| <= ulp(hi)/2
-  FMT_TC = 3,    // tensor-core B operand: bf16 planes [Nf][hi, lo][J][ldn], see TcShape
+  FMT_TC = 3,    // spectra for the tensor cores: channel-major float2 T[K][ldn][Nf], packed
+                 // afterwards into the bf16 B operand planes [Nf][hi, lo][J][ldn] (TcShape)
 };
 
 // Arithmetic used by the per-frequency block matvec (phase 3).
@@ -57,7 +58,6 @@ struct FwdDesc {
   int64_t X_ld_w, X_ld_row, X_ld_b;     // complex-element strides of X
   int fmt;                 // CFmt of X
   int pad_single;          // round the loaded input to FP32 (pad phase in FP32)
-  int tc_KC, tc_N, tc_J;   // FMT_TC only: right-hand sides per chunk, MMA N, rows per plane
 };
 
 // Inverse real FFT of Hermitian half spectra followed by unpad (phases 4-5 fused).
@@ -108,6 +108,10 @@ struct TcDesc {
   unsigned int* status;
 };
 cudaError_t launch_tc_gemm_n(const TcDesc& d, cudaStream_t s);
+// T[K][ldn][Nf] float2 -> B planes [Nf][2][J][ldn] bf16 (hi, lo) for K right-hand sides
+cudaError_t launch_tc_pack(const void* T, void* B, int K, int Nf, int ldn, cudaStream_t s);
+size_t tc_operand_bytes(int K, int Nf, int ldn);   // B planes
+size_t tc_spectrum_bytes(int K, int Nf, int ldn);  // T
 cudaError_t launch_convert_bf16x2(const double2* master, void* out, int Nf, int Nd, int ldn, cudaStream_t s);
 size_t tc_smem_bytes(int N);
 

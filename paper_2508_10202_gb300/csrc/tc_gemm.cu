@@ -286,6 +286,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// Channel-major spectra T[b][n][w] (the FFT's natural order) -> tensor-core B
+// planes [w][hi, lo][row][n] through a 64-channel x 32-frequency shared-memory
+// tile: reads cover 32 consecutive frequencies of a channel, writes 64
+// consecutive channels (128 bytes of bf16) of one B row.
+constexpr int PK_N = 64, PK_W = 32;
+__global__ void __launch_bounds__(256) tc_pack_kernel(const float2* __restrict__ T, __nv_bfloat16* __restrict__ B,
+                                                      int K, int Nf, int ldn, int KC, int N, int J) {
+  __shared__ float2 tile[PK_N][PK_W + 1];
+  const int n0 = blockIdx.x * PK_N, w0 = blockIdx.y * PK_W, b = blockIdx.z;
+  const float2* src = T + (int64_t)b * ldn * Nf;
+  for (int i = threadIdx.x; i < PK_N * PK_W; i += 256) {
+    const int nn = i / PK_W, ww = i - nn * PK_W;
+    const int n = n0 + nn, w = w0 + ww;
+    tile[nn][ww] = (n < ldn && w < Nf) ? src[(int64_t)n * Nf + w] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int ch = b / KC, q = b - ch * KC;
+  const int jr = ch * N + q, ji = jr + KC;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n = n0 + 2 * lane;
+  for (int sgm = warp; sgm < PK_W * 4; sgm += 8) {   // (frequency, row type) segments
+    const int ww = sgm / 4, rt = sgm % 4;
+    const int w = w0 + ww;
+    if (w >= Nf || n >= ldn) continue;
+    const float2 a = tile[2 * lane][ww], c = tile[2 * lane + 1][ww];
+    const float va = rt < 2 ? a.x : a.y, vc = rt < 2 ? c.x : c.y;   // Re rows, then Im rows
+    const __nv_bfloat16 ha = __float2bfloat16(va), hc = __float2bfloat16(vc);
+    __nv_bfloat162 out;
+    if (rt % 2 == 0) {
+      out.x = ha;
+      out.y = hc;
+    } else {
+      out.x = __float2bfloat16(va - __bfloat162float(ha));
+      out.y = __float2bfloat16(vc - __bfloat162float(hc));
+    }
+    const int row = rt < 2 ? jr : ji, plane = rt % 2;
+    *reinterpret_cast<__nv_bfloat162*>(B + (((int64_t)w * 2 + plane) * J + row) * ldn + n) = out;
+  }
+}
+
 // master FP64 F-hat [Nf][Nd][ldn] -> four bf16 planes [Nf][4][Nd][ldn]: Re hi, Re lo, Im hi, Im lo
 __global__ void convert_bf16x2_kernel(const double2* __restrict__ in, __nv_bfloat16* __restrict__ out, int Nd, int ldn,
                                       int64_t n) {
@@ -352,6 +392,18 @@ cudaError_t launch_convert_bf16x2(const double2* master, void* out, int Nf, int 
   const int64_t want = (n + threads - 1) / threads;
   const int blocks = (int)(want < 152 * 32 ? want : 152 * 32);
   convert_bf16x2_kernel<<<blocks, threads, 0, s>>>(master, static_cast<__nv_bfloat16*>(out), Nd, ldn, n);
+  return cudaGetLastError();
+}
+
+size_t tc_operand_bytes(int K, int Nf, int ldn) { return (size_t)Nf * 2 * tc_shape(K).J * ldn * 2; }
+size_t tc_spectrum_bytes(int K, int Nf, int ldn) { return (size_t)K * ldn * Nf * sizeof(float2); }
+
+cudaError_t launch_tc_pack(const void* T, void* B, int K, int Nf, int ldn, cudaStream_t s) {
+  if (K == 0) return cudaSuccess;
+  const TcShape t = tc_shape(K);
+  dim3 grid((ldn + PK_N - 1) / PK_N, (Nf + PK_W - 1) / PK_W, K);
+  tc_pack_kernel<<<grid, 256, 0, s>>>(static_cast<const float2*>(T), static_cast<__nv_bfloat16*>(B), K, Nf, ldn, t.KC,
+                                      t.N, t.J);
   return cudaGetLastError();
 }
 
