@@ -298,52 +298,63 @@ def time_variant(torch, op, mt, dt, yt, xt, stream, pf, pa, steps: int) -> dict:
             "phase_ms_F": [v / nf for v in tf], "phase_ms_Fstar": [v / na for v in ta]}
 
 
-def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, K: int = 64, steps: int = 10) -> dict:
-    """K right-hand sides through F at once (FP32 phases, block matvec on the
-    tensor cores with bf16 hi/lo F-hat), the multi-RHS workload."""
+def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: int = 64, steps: int = 10) -> dict:
+    """K right-hand sides through F (or F*) at once: FP32 phases, block matvec on
+    the tensor cores with bf16 hi/lo F-hat, the multi-RHS workload."""
     import numpy as np
 
     import synth
     Nt, Nd, Nm = Fcol.shape
-    m = synth.vectors(synth.TAG_M, Nt, Nm, k=K, seed=7, dtype=np.float32)
-    mt = torch.from_numpy(m).to(dev)
-    yt = torch.empty((K, Nt, Nd), dtype=torch.float32, device=dev)
-    op.set_precision("F", "sssss", "bf16x2")
+    fwd = which == "F"
+    n_in, n_out = (Nm, Nd) if fwd else (Nd, Nm)
+    x = synth.vectors(synth.TAG_M if fwd else synth.TAG_D, Nt, n_in, k=K, seed=7, dtype=np.float32)
+    xt = torch.from_numpy(x).to(dev)
+    yt = torch.empty((K, Nt, n_out), dtype=torch.float32, device=dev)
+    op.set_precision(which, "sssss", "bf16x2")
+    call = op.matvec if fwd else op.rmatvec
     for _ in range(2):
-        op.matvec(mt, out=yt, stream=stream)
+        call(xt, out=yt, stream=stream)
     torch.cuda.synchronize()
     op.reset_timing()
     op.set_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        op.matvec(mt, out=yt, stream=stream)
+        call(xt, out=yt, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     op.set_timing(False)
     ms = e0.elapsed_time(e1) / steps
-    ph, n = op.phase_times("F")
+    ph, n = op.phase_times(which)
     ph = [v / n for v in ph]
     y = yt.cpu().numpy()
     rng = np.random.default_rng(5)
     got, ref = [], []
     for b in rng.choice(K, size=min(K, 6), replace=False):
-        idx = [(int(rng.integers(Nt)), int(rng.integers(Nd))) for _ in range(6)]
-        ref += list(oracle_entries(Fcol, m[b].astype(np.float64), idx))
+        idx = [(int(rng.integers(Nt)), int(rng.integers(n_out))) for _ in range(6)]
+        if fwd:
+            ref += list(oracle_entries(Fcol, x[b].astype(np.float64), idx))
+        else:
+            ref += list(oracle_rentries(Fcol, x[b].astype(np.float64), idx))
         got += [float(y[b, i, r]) for i, r in idx]
     got, ref = np.array(got), np.array(ref)
     err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    Nf, ldn = Nt + 1, (Nm + 7) // 8 * 8
+    Nf, ldn, ldr = Nt + 1, (Nm + 7) // 8 * 8, (Nd + 7) // 8 * 8
     a_bytes = Nf * 4 * Nd * ldn * 2                    # bf16 hi/lo planes of F-hat
-    b_bytes = Nf * 2 * 2 * K * ldn * 2                 # bf16 hi/lo [Re M | Im M]
+    # bf16 hi/lo [Re X | Im X] in, complex FP32 spectra out
+    io_bytes = (Nf * 2 * 2 * K * ldn * 2 + K * Nf * Nd * 8) if fwd else (Nf * 2 * 2 * K * ldr * 2 + K * Nf * ldn * 8)
     tc_s = ph[1] * 1e-3
-    flops_exec = 6 * 2 * 128 * (2 * K) * ldn * Nf * ((Nd + 127) // 128)
+    if fwd:   # M = Nd rows per 128-row tile, contraction over ldn
+        flops_exec = 6 * 2 * 128 * (2 * K) * ldn * Nf * ((Nd + 127) // 128)
+    else:     # M = Nm rows, contraction over Nd in 64-wide steps
+        flops_exec = 6 * 2 * 128 * (2 * K) * ((Nd + 63) // 64 * 64) * Nf * ((Nm + 127) // 128)
     hbm, _ = peaks
     bf16_peak = load_tensor_peak()
-    return {"K": K, "prec": "sssss/bf16x2 (tcgen05, bf16 hi+lo, FP32 accumulate)", "ms_call": ms,
+    tb = a_bytes + io_bytes
+    return {"which": which, "K": K, "prec": "sssss/bf16x2 (tcgen05, bf16 hi+lo, FP32 accumulate)", "ms_call": ms,
             "matvec_s": K / (ms * 1e-3), "phase_ms": ph, "rel_err_sampled": err,
-            "tc_kernel": {"hbm_bytes": a_bytes + b_bytes, "achieved_GBs": (a_bytes + b_bytes) / tc_s / 1e9,
-                          "hbm_frac": (a_bytes + b_bytes) / tc_s / 1e9 / hbm,
+            "tc_kernel": {"hbm_bytes": tb, "achieved_GBs": tb / tc_s / 1e9,
+                          "hbm_frac": tb / tc_s / 1e9 / hbm,
                           "tensor_TFLOPs_executed": flops_exec / tc_s / 1e12,
                           "tensor_frac": flops_exec / tc_s / 1e12 / bf16_peak,
                           "useful_TFLOPs": 8.0 * Nf * Nd * Nm * K / tc_s / 1e12},
@@ -435,6 +446,11 @@ def bench_pareto(torch, op, mt, dt, yt, xt, stream) -> dict:
 def oracle_entries(Fcol, m, idx):
     import oracle
     return oracle.matvec_entries(Fcol, m, idx)
+
+
+def oracle_rentries(Fcol, d, idx):
+    import oracle
+    return oracle.rmatvec_entries(Fcol, d, idx)
 
 
 def load_tensor_peak() -> float:
@@ -570,7 +586,7 @@ def main(args) -> None:
 
     multi = None
     if rank == 0 and not args.no_multi:
-        multi = bench_multi_rhs(torch, op, Fcol, dev, stream, (peak, peak_kind))
+        multi = {w: bench_multi_rhs(torch, op, Fcol, dev, stream, (peak, peak_kind), which=w) for w in ("F", "F*")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -70,8 +70,8 @@ typedef enum { FFTMV_F64 = 0, FFTMV_F32 = 1 } fftmv_phase_prec;
  *              48 significant bits), double-float arithmetic on the FP32
  *              pipe.  Not native FP64: an FP64-class emulation for GPUs whose
  *              FP64 rate cannot keep pace with memory (GB300).
- *   BF16X2   : gemv=F32 only, F (FFTMV_FORWARD) only.  Many right-hand sides
- *              on the tensor cores (tcgen05): F-hat and the transformed inputs
+ *   BF16X2   : gemv=F32 only.  Many right-hand sides, F and F*, on the
+ *              tensor cores (tcgen05): F-hat and the transformed inputs
  *              split into bfloat16 hi + lo parts (about 16 significant bits),
  *              hi*hi + hi*lo + lo*hi accumulated in FP32.  Pays off once K is
  *              large (tens of right-hand sides); its error is at FP32 level. */

@@ -204,9 +204,10 @@ CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
   c.Cout = fwd ? op->Nd : op->Nm;
   c.in_ld = fwd ? op->ldn : op->Nd;
   c.out_ld = fwd ? op->Nd : op->ldn;
-  if (c.kind == GEMV_TC) {  // B operand planes [Nf][2][J][ldn] bf16, then the channel-major spectra
-    c.in_hat = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)op->ldn)) +
-               align256(tc_spectrum_bytes((int)K, (int)op->Nf, (int)op->ldn));
+  if (c.kind == GEMV_TC) {  // B operand planes [Nf][2][J][ld] bf16, then the channel-major spectra
+    if (!fwd) c.in_ld = (op->Nd + 7) / 8 * 8;   // d-hat channels padded like the rows of F-hat
+    c.in_hat = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld)) +
+               align256(tc_spectrum_bytes((int)K, (int)op->Nf, (int)c.in_ld));
   } else {
     c.in_hat = align256((size_t)K * op->Nf * c.in_ld * fmt_bytes(c.in_fmt));
   }
@@ -245,14 +246,14 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   void* tc_T = nullptr;
   if (c.kind == GEMV_TC) {
     const TcShape t = tc_shape((int)K);
-    const size_t bbytes = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)op->ldn));
+    const size_t bbytes = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld));
     tc_T = static_cast<char*>(in_hat) + bbytes;
     f.X = tc_T;
     // B rows no right-hand side fills (chunk padding, a short last chunk) must read as zero
     if (2 * t.KC < t.N || (int)K % t.KC != 0) e = cudaMemsetAsync(in_hat, 0, bbytes, s);
   }
   if (e == cudaSuccess) e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fprec, s);
-  if (e == cudaSuccess && tc_T) e = launch_tc_pack(tc_T, in_hat, (int)K, (int)op->Nf, (int)op->ldn, s);
+  if (e == cudaSuccess && tc_T) e = launch_tc_pack(tc_T, in_hat, (int)K, (int)op->Nf, (int)c.in_ld, s);
   if (ev) cudaEventRecord(ev[1], s);
   if (e == cudaSuccess) {
     GemvDesc g{};
@@ -273,11 +274,14 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
       t.y = out_hat;
       t.Nf = (int)op->Nf;
       t.Nd = (int)op->Nd;
+      t.Nm = (int)op->Nm;
       t.ldn = (int)op->ldn;
+      t.ldr = (int)((op->Nd + 7) / 8 * 8);
       t.K = (int)K;
+      t.adjoint = !fwd;
       t.y_ld_b = op->Nf * c.out_ld;
       t.status = op->status;
-      e = launch_tc_gemm_n(t, s);
+      e = launch_tc_gemm(t, s);
     } else {
       e = fwd ? launch_gemv_n(c.kind, g, s) : launch_gemv_h(c.kind, g, s);
     }
@@ -517,8 +521,6 @@ int fftmv_set_precision(fftmv_op* op, int which, const fftmv_precision* prec) {
   if (rc) return rc;
   if (which != FFTMV_FORWARD && which != FFTMV_ADJOINT) return fail(FFTMV_EINVAL, "which=%d is not F/F*", which);
   if ((rc = check_prec(prec))) return rc;
-  if (prec->gemv_mode == FFTMV_GEMV_BF16X2 && which != FFTMV_FORWARD)
-    return fail(FFTMV_EUNSUPPORTED, "gemv_mode BF16X2 (tensor cores) is built for F only");
   DeviceGuard dg(op->device);
   const int kind = gemv_kind(*prec);
   const size_t n = (size_t)op->Nf * op->Nd * op->ldn;

@@ -101,13 +101,14 @@ TcShape tc_shape(int K);
 
 struct TcDesc {
   const void* A;           // bf16 planes [Nf][4][Nd][ldn] (Re hi, Re lo, Im hi, Im lo)
-  const void* B;           // bf16 planes [Nf][2][J][ldn]
-  void* y;                 // FMT_C64 [K][Nf][Nd]
-  int Nf, Nd, ldn, K;
+  const void* B;           // bf16 planes [Nf][2][J][ldk], ldk = ldn (F) or ldr (F*)
+  void* y;                 // FMT_C64 [K][Nf][Nd] (F) or [K][Nf][ldn] (F*)
+  int Nf, Nd, Nm, ldn, ldr, K;
+  int adjoint;             // 0: F (contract over n), 1: F* (contract over r, A read transposed)
   int64_t y_ld_b;
   unsigned int* status;
 };
-cudaError_t launch_tc_gemm_n(const TcDesc& d, cudaStream_t s);
+cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s);
 // T[K][ldn][Nf] float2 -> B planes [Nf][2][J][ldn] bf16 (hi, lo) for K right-hand sides
 cudaError_t launch_tc_pack(const void* T, void* B, int K, int Nf, int ldn, cudaStream_t s);
 size_t tc_operand_bytes(int K, int Nf, int ldn);   // B planes

@@ -72,6 +72,19 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(const void* smem) {
   return d;
 }
 
+// shared-memory matrix descriptor: MN-major, 128-byte swizzle.  A 128 x 64
+// tile is two 64-wide MN halves 8 KB apart (leading byte offset), each 64 K
+// rows of 128 bytes; K groups of 8 rows are 1024 B apart (stride byte offset).
+__device__ __forceinline__ uint64_t umma_desc_mn_sw128(const void* smem) {
+  const uint64_t addr = smem_u32(smem);
+  uint64_t d = (addr & 0x3FFFFull) >> 4;
+  d |= (uint64_t)(8192 >> 4) << 16;         // leading byte offset: next 64-wide MN half
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row K group
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = n
 __host__ __device__ constexpr uint32_t umma_idesc_bf16(int n) {
   return (1u << 4)                         // D format: F32
@@ -123,14 +136,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 struct TcArgs {
-  int Nf, Nd, ldn, K, KC, N, nkb;
-  int64_t y_ld_b;           // complex elements between right-hand sides of y
-  float2* y;                // D-hat [K][Nf][Nd] (FMT_C64)
+  int Nf, M, K, KC, N, nkb;  // M: output rows (Nd for F, Nm for F*)
+  int64_t y_ld_b, y_ld_w;    // complex elements between right-hand sides / frequencies of y
+  float2* y;                 // [K][Nf][rows] (FMT_C64)
   unsigned int* status;
 };
 
+// H = false: F, A = F-hat_w (rows r, K along n, K-major).
+// H = true:  F*, A = F-hat_w^T (rows n, K along r, MN-major: the same planes read
+//            transposed); the conjugate enters through the epilogue signs.
+template <bool H>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_gemm_n_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned tile area (the 128-byte swizzle pattern repeats every 1024 bytes)
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -180,7 +197,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         unsigned char* st = tiles + s * stage_bytes;
         mbar_arrive_expect_tx(&full[s], stage_bytes);
-        for (int p = 0; p < 4; ++p) tma_load_4d(st + p * a_plane, &mapA, kb * TC_BK, m0, p, w, &full[s]);
+        for (int p = 0; p < 4; ++p) {
+          if constexpr (H) {  // two 64 (n) x 64 (r) boxes per plane
+            tma_load_4d(st + p * a_plane, &mapA, m0, kb * TC_BK, p, w, &full[s]);
+            tma_load_4d(st + p * a_plane + a_plane / 2, &mapA, m0 + 64, kb * TC_BK, p, w, &full[s]);
+          } else {
+            tma_load_4d(st + p * a_plane, &mapA, kb * TC_BK, m0, p, w, &full[s]);
+          }
+        }
         for (int p = 0; p < 2; ++p) tma_load_4d(st + 4 * a_plane + p * b_plane, &mapB, kb * TC_BK, ch * N, p, w, &full[s]);
       }
       for (int kk = max(0, kb - TC_STAGES); kk < kb; ++kk)
@@ -188,7 +212,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = umma_idesc_bf16(N);
+      const uint32_t idesc = umma_idesc_bf16(N) | (H ? (1u << 15) : 0u);   // bit 15: A is MN-major
       for (int kb = 0; kb < a.nkb && ok; ++kb) {
         const int g = kb / TC_GROUP, set = g & 1;
         const bool first = kb % TC_GROUP == 0;
@@ -208,10 +232,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int ks = 0; ks < TC_BK / 16; ++ks) {
           // +32 bytes per 16 bf16 along K inside the swizzled row: +2 in the address field
-          const uint64_t frh = umma_desc_sw128(st + 0 * a_plane) + 2 * ks;
-          const uint64_t frl = umma_desc_sw128(st + 1 * a_plane) + 2 * ks;
-          const uint64_t fih = umma_desc_sw128(st + 2 * a_plane) + 2 * ks;
-          const uint64_t fil = umma_desc_sw128(st + 3 * a_plane) + 2 * ks;
+          // A: K-major advances 32 B per 16 K inside the swizzled row; MN-major
+          // advances two 8-row K groups (2048 B)
+          const uint64_t ak = H ? (uint64_t)(2048 >> 4) * ks : 2 * ks;
+          const uint64_t frh = (H ? umma_desc_mn_sw128(st + 0 * a_plane) : umma_desc_sw128(st + 0 * a_plane)) + ak;
+          const uint64_t frl = (H ? umma_desc_mn_sw128(st + 1 * a_plane) : umma_desc_sw128(st + 1 * a_plane)) + ak;
+          const uint64_t fih = (H ? umma_desc_mn_sw128(st + 2 * a_plane) : umma_desc_sw128(st + 2 * a_plane)) + ak;
+          const uint64_t fil = (H ? umma_desc_mn_sw128(st + 3 * a_plane) : umma_desc_sw128(st + 3 * a_plane)) + ak;
           const uint64_t bh = umma_desc_sw128(st + 4 * a_plane) + 2 * ks;
           const uint64_t bl = umma_desc_sw128(st + 4 * a_plane + b_plane) + 2 * ks;
           const uint32_t acc = !(first && ks == 0);
@@ -255,8 +282,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tmem_ld16(t2 + KC + q0, a2i);   // Im F * Im M
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            sre[c * 16 + i] += a1r[i] - a2i[i];
-            sim[c * 16 + i] += a1i[i] + a2r[i];
+            if constexpr (H) {  // conj(F) M: Re = ReF ReM + ImF ImM, Im = ReF ImM - ImF ReM
+              sre[c * 16 + i] += a1r[i] + a2i[i];
+              sim[c * 16 + i] += a1i[i] - a2r[i];
+            } else {
+              sre[c * 16 + i] += a1r[i] - a2i[i];
+              sim[c * 16 + i] += a1i[i] + a2r[i];
+            }
           }
         }
       }
@@ -264,7 +296,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&drained[set]);
     }
-    if (ok && row < a.Nd) {
+    if (ok && row < a.M) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
 #pragma unroll
@@ -272,7 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int q = qlo + c * 16 + i;
           const int b = ch * KC + q;
           if (c * 16 + i < qn && b < a.K)
-            a.y[b * a.y_ld_b + (int64_t)w * a.Nd + row] = make_float2(sre[c * 16 + i], sim[c * 16 + i]);
+            a.y[b * a.y_ld_b + (int64_t)w * a.y_ld_w + row] = make_float2(sre[c * 16 + i], sim[c * 16 + i]);
         }
       }
     }
@@ -407,30 +439,33 @@ cudaError_t launch_tc_pack(const void* T, void* B, int K, int Nf, int ldn, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_gemm_n(const TcDesc& d, cudaStream_t s) {
+cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s) {
   if (d.Nf == 0 || d.K == 0) return cudaSuccess;
   const TcShape t = tc_shape(d.K);
+  const bool H = d.adjoint != 0;
+  const int ldk = H ? d.ldr : d.ldn;   // contraction length (padded) of the B operand
   CUtensorMap mapA, mapB;
-  cudaError_t e = make_map(&mapA, d.A, (uint64_t)d.ldn, (uint64_t)d.Nd, 4, (uint64_t)d.Nf, TC_M);
+  cudaError_t e = make_map(&mapA, d.A, (uint64_t)d.ldn, (uint64_t)d.Nd, 4, (uint64_t)d.Nf, H ? 64 : TC_M);
   if (e != cudaSuccess) return e;
-  e = make_map(&mapB, d.B, (uint64_t)d.ldn, (uint64_t)t.J, 2, (uint64_t)d.Nf, (uint32_t)t.N);
+  e = make_map(&mapB, d.B, (uint64_t)ldk, (uint64_t)t.J, 2, (uint64_t)d.Nf, (uint32_t)t.N);
   if (e != cudaSuccess) return e;
   TcArgs a{};
   a.Nf = d.Nf;
-  a.Nd = d.Nd;
-  a.ldn = d.ldn;
+  a.M = H ? d.Nm : d.Nd;
   a.K = d.K;
   a.KC = t.KC;
   a.N = t.N;
-  a.nkb = (d.ldn + TC_BK - 1) / TC_BK;
+  a.nkb = H ? (d.Nd + TC_BK - 1) / TC_BK : (d.ldn + TC_BK - 1) / TC_BK;
   a.y_ld_b = d.y_ld_b;
+  a.y_ld_w = H ? d.ldn : d.Nd;
   a.y = static_cast<float2*>(d.y);
   a.status = d.status;
   const size_t smem = tc_smem_bytes(t.N);
-  e = cudaFuncSetAttribute(tc_gemm_n_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kernel = H ? tc_gemm_kernel<true> : tc_gemm_kernel<false>;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(d.Nf, t.nch, (d.Nd + TC_M - 1) / TC_M);
-  tc_gemm_n_kernel<<<grid, TC_THREADS, smem, s>>>(mapA, mapB, a);
+  dim3 grid(d.Nf, t.nch, (a.M + TC_M - 1) / TC_M);
+  kernel<<<grid, TC_THREADS, smem, s>>>(mapA, mapB, a);
   return cudaGetLastError();
 }
 
