@@ -1,0 +1,763 @@
+// Batched real FFTs along time for the block-Toeplitz matvec (Section 2.4,
+// phases 1-2 and 4-5 of the paper's algorithm), written for sm_103a.
+//
+// A CTA transforms NP pairs of real channels; pair (c, c+1) is the complex
+// signal z = x_c + i x_{c+1}, and the real-to-complex split is done in the
+// epilogue (forward) or the Hermitian assembly in the prologue (inverse).  The
+// complex FFT of length L = 2^a 3^b 5^c is a Stockham auto-sort sequence of
+// radix-2, 3, 4, 5, 8 passes, so the result lands in natural order with no bit
+// reversal.  The passes run in place on one shared-memory buffer (each thread
+// holds its butterflies in registers across a barrier), which leaves room for
+// 2 NP channels per CTA: a time step of them is 32 to 64 contiguous bytes of
+// HBM.  Twiddles come from a per-length table exp(-2 pi i j / L) built once on
+// the host.
+//
+// Zero padding (phase 1) and unpadding (phase 5) are fused into the first and
+// last radix passes: samples t >= Nt are never read from HBM, and only t < Nt
+// is written back.  Casts between the I/O dtype, the pad/unpad precision and the
+// FFT precision are fused into the loads and stores (Section 3.2).
+//
+// Arithmetic.  The same transform is instantiated for three precisions:
+//   double : FP64 FMA (GB300 runs it at ~1.2 TFLOP/s, so FP64 FFTs are
+//            FP64-pipe bound);
+//   float  : FP32;
+//   DFP    : double-float, an FP64-class format on the FP32 pipe.  A real is
+//            an unevaluated pair hi + lo of floats (|lo| <= ulp(hi)/2, about
+//            48 significant bits); sums use TwoSum + Fast2Sum renormalisation,
+//            products an FMA-exact TwoProd plus the hi*lo cross terms.  The
+//            adds are the normwise-accurate ("sloppy") double-word sums, which
+//            is the accuracy an FFT's normwise error analysis needs.
+
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
+#include "fftmv_internal.h"
+
+namespace fftmv {
+namespace {
+
+struct DFP {};  // precision tag: double-float on the FP32 pipe
+
+// a real constant in every precision: FP64 value and its FP32 hi/lo split
+struct Kc {
+  double d;
+  float h, l;
+};
+// cos/sin of 2 pi / 5, 4 pi / 5, pi / 3 and 1 / sqrt(2)
+__device__ constexpr Kc KC1{0.30901699437494742410, 0.30901700258255005f, -8.207602597565256e-09f};
+__device__ constexpr Kc KC2{-0.80901699437494742410, -0.80901700258255f, 8.207602597565256e-09f};
+__device__ constexpr Kc KS1{0.95105651629515357212, 0.9510565400123596f, -2.3717205976936384e-08f};
+__device__ constexpr Kc KS2{0.58778525229247312917, 0.5877852439880371f, 8.304436249773062e-09f};
+__device__ constexpr Kc KS3{0.86602540378443864676, 0.8660253882408142f, 1.5543625053737742e-08f};
+__device__ constexpr Kc KR2{0.70710678118654752440, 0.7071067690849304f, 1.2101617485882343e-08f};
+
+// ---------------------------------------------------------------------------
+// double-float reals
+// ---------------------------------------------------------------------------
+struct dfr {
+  float h, l;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ dfr fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dfr{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfr df_add(dfr a, dfr b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  return fast_two_sum(s, e);
+}
+__device__ __forceinline__ dfr df_neg(dfr a) { return dfr{-a.h, -a.l}; }
+__device__ __forceinline__ dfr df_mul(dfr a, dfr b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+// a.re*b.re - s*a.im*b.im (s = +1) in one renormalisation
+__device__ __forceinline__ dfr df_dot2(dfr a, dfr b, dfr c, dfr d, float sgn) {
+  // a*b + sgn*c*d
+  const float p1 = __fmul_rn(a.h, b.h);
+  const float p2 = __fmul_rn(sgn * c.h, d.h);
+  float e1 = __fmaf_rn(a.h, b.h, -p1);
+  float e2 = __fmaf_rn(sgn * c.h, d.h, -p2);
+  float s, t;
+  two_sum(p1, p2, s, t);
+  t = __fadd_rn(t, __fadd_rn(e1, e2));
+  t = __fmaf_rn(a.h, b.l, t);
+  t = __fmaf_rn(a.l, b.h, t);
+  t = __fmaf_rn(sgn * c.h, d.l, t);
+  t = __fmaf_rn(sgn * c.l, d.h, t);
+  return fast_two_sum(s, t);
+}
+
+// ---------------------------------------------------------------------------
+// arithmetic traits: reals R, complexes C (the shared-memory element)
+// ---------------------------------------------------------------------------
+template <typename P> struct Ar;
+
+template <> struct Ar<double> {
+  using R = double;
+  using C = double2;
+  __device__ __forceinline__ static R add(R a, R b) { return a + b; }
+  __device__ __forceinline__ static R sub(R a, R b) { return a - b; }
+  __device__ __forceinline__ static R neg(R a) { return -a; }
+  __device__ __forceinline__ static R half(R a) { return 0.5 * a; }
+  __device__ __forceinline__ static R mulk(R a, const Kc& k) { return a * k.d; }
+  __device__ __forceinline__ static R re(C c) { return c.x; }
+  __device__ __forceinline__ static R im(C c) { return c.y; }
+  __device__ __forceinline__ static C mk(R r, R i) { return make_double2(r, i); }
+  __device__ __forceinline__ static C cmul(C a, C w) {
+    return make_double2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+  }
+  __device__ __forceinline__ static C conj(C a) { return make_double2(a.x, -a.y); }
+  __device__ __forceinline__ static R from_d(double x) { return x; }
+  __device__ __forceinline__ static R from_f(float x) { return x; }
+  __device__ __forceinline__ static double to_d(R x) { return x; }
+  __device__ __forceinline__ static float to_f(R x) { return (float)x; }
+  __device__ __forceinline__ static R zero() { return 0.0; }
+};
+
+template <> struct Ar<float> {
+  using R = float;
+  using C = float2;
+  __device__ __forceinline__ static R add(R a, R b) { return a + b; }
+  __device__ __forceinline__ static R sub(R a, R b) { return a - b; }
+  __device__ __forceinline__ static R neg(R a) { return -a; }
+  __device__ __forceinline__ static R half(R a) { return 0.5f * a; }
+  __device__ __forceinline__ static R mulk(R a, const Kc& k) { return a * (float)k.d; }
+  __device__ __forceinline__ static R re(C c) { return c.x; }
+  __device__ __forceinline__ static R im(C c) { return c.y; }
+  __device__ __forceinline__ static C mk(R r, R i) { return make_float2(r, i); }
+  __device__ __forceinline__ static C cmul(C a, C w) {
+    return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+  }
+  __device__ __forceinline__ static C conj(C a) { return make_float2(a.x, -a.y); }
+  __device__ __forceinline__ static R from_d(double x) { return (float)x; }
+  __device__ __forceinline__ static R from_f(float x) { return x; }
+  __device__ __forceinline__ static double to_d(R x) { return x; }
+  __device__ __forceinline__ static float to_f(R x) { return x; }
+  __device__ __forceinline__ static R zero() { return 0.f; }
+};
+
+// complex double-float stored as float4 (re_hi, im_hi, re_lo, im_lo): the
+// FMT_DF layout, so spectra move between phases without conversion
+template <> struct Ar<DFP> {
+  using R = dfr;
+  using C = float4;
+  __device__ __forceinline__ static R add(R a, R b) { return df_add(a, b); }
+  __device__ __forceinline__ static R sub(R a, R b) { return df_add(a, df_neg(b)); }
+  __device__ __forceinline__ static R neg(R a) { return df_neg(a); }
+  __device__ __forceinline__ static R half(R a) { return dfr{0.5f * a.h, 0.5f * a.l}; }
+  __device__ __forceinline__ static R mulk(R a, const Kc& k) { return df_mul(a, dfr{k.h, k.l}); }
+  __device__ __forceinline__ static R re(C c) { return dfr{c.x, c.z}; }
+  __device__ __forceinline__ static R im(C c) { return dfr{c.y, c.w}; }
+  __device__ __forceinline__ static C mk(R r, R i) { return make_float4(r.h, i.h, r.l, i.l); }
+  __device__ __forceinline__ static C cmul(C a, C w) {
+    const dfr ar = re(a), ai = im(a), wr = re(w), wi = im(w);
+    return mk(df_dot2(ar, wr, ai, wi, -1.f), df_dot2(ar, wi, ai, wr, 1.f));
+  }
+  __device__ __forceinline__ static C conj(C a) { return make_float4(a.x, -a.y, a.z, -a.w); }
+  __device__ __forceinline__ static R from_d(double x) {
+    const float h = (float)x;
+    return dfr{h, (float)(x - (double)h)};
+  }
+  __device__ __forceinline__ static R from_f(float x) { return dfr{x, 0.f}; }
+  __device__ __forceinline__ static double to_d(R x) { return (double)x.h + (double)x.l; }
+  __device__ __forceinline__ static float to_f(R x) { return __fadd_rn(x.h, x.l); }
+  __device__ __forceinline__ static R zero() { return dfr{0.f, 0.f}; }
+};
+
+// complex helpers built on the traits
+template <typename P> struct Cx {
+  using A = Ar<P>;
+  using C = typename A::C;
+  __device__ __forceinline__ static C add(C a, C b) { return A::mk(A::add(A::re(a), A::re(b)), A::add(A::im(a), A::im(b))); }
+  __device__ __forceinline__ static C sub(C a, C b) { return A::mk(A::sub(A::re(a), A::re(b)), A::sub(A::im(a), A::im(b))); }
+  __device__ __forceinline__ static C mulk(C a, const Kc& k) { return A::mk(A::mulk(A::re(a), k), A::mulk(A::im(a), k)); }
+  // multiply by -i (forward) or +i (inverse)
+  template <bool INV> __device__ __forceinline__ static C mmi(C a) {
+    return INV ? A::mk(A::neg(A::im(a)), A::re(a)) : A::mk(A::im(a), A::neg(A::re(a)));
+  }
+};
+
+// In-register DFT of size R: X_p = sum_q v_q exp(-+2 pi i q p / R).
+template <typename P, int R, bool INV> struct Dft;
+
+template <typename P, bool INV> struct Dft<P, 2, INV> {
+  using C = typename Ar<P>::C;
+  __device__ __forceinline__ static void run(C* v) {
+    const C a = v[0], b = v[1];
+    v[0] = Cx<P>::add(a, b);
+    v[1] = Cx<P>::sub(a, b);
+  }
+};
+
+template <typename P, bool INV> struct Dft<P, 3, INV> {
+  using A = Ar<P>;
+  using C = typename A::C;
+  __device__ __forceinline__ static void run(C* v) {
+    const C s = Cx<P>::add(v[1], v[2]);
+    const C d = Cx<P>::mulk(Cx<P>::template mmi<INV>(Cx<P>::sub(v[1], v[2])), KS3);
+    const C m = A::mk(A::sub(A::re(v[0]), A::half(A::re(s))), A::sub(A::im(v[0]), A::half(A::im(s))));
+    v[0] = Cx<P>::add(v[0], s);
+    v[1] = Cx<P>::add(m, d);
+    v[2] = Cx<P>::sub(m, d);
+  }
+};
+
+template <typename P, bool INV> struct Dft<P, 4, INV> {
+  using C = typename Ar<P>::C;
+  __device__ __forceinline__ static void run(C* v) {
+    const C a = Cx<P>::add(v[0], v[2]), b = Cx<P>::sub(v[0], v[2]);
+    const C c = Cx<P>::add(v[1], v[3]), d = Cx<P>::template mmi<INV>(Cx<P>::sub(v[1], v[3]));
+    v[0] = Cx<P>::add(a, c);
+    v[2] = Cx<P>::sub(a, c);
+    v[1] = Cx<P>::add(b, d);
+    v[3] = Cx<P>::sub(b, d);
+  }
+};
+
+template <typename P, bool INV> struct Dft<P, 5, INV> {
+  using C = typename Ar<P>::C;
+  __device__ __forceinline__ static void run(C* v) {
+    const C a1 = Cx<P>::add(v[1], v[4]), b1 = Cx<P>::sub(v[1], v[4]);
+    const C a2 = Cx<P>::add(v[2], v[3]), b2 = Cx<P>::sub(v[2], v[3]);
+    const C x0 = v[0];
+    const C r1 = Cx<P>::add(x0, Cx<P>::add(Cx<P>::mulk(a1, KC1), Cx<P>::mulk(a2, KC2)));
+    const C r2 = Cx<P>::add(x0, Cx<P>::add(Cx<P>::mulk(a1, KC2), Cx<P>::mulk(a2, KC1)));
+    const C j1 = Cx<P>::template mmi<INV>(Cx<P>::add(Cx<P>::mulk(b1, KS1), Cx<P>::mulk(b2, KS2)));
+    const C j2 = Cx<P>::template mmi<INV>(Cx<P>::sub(Cx<P>::mulk(b1, KS2), Cx<P>::mulk(b2, KS1)));
+    v[0] = Cx<P>::add(x0, Cx<P>::add(a1, a2));
+    v[1] = Cx<P>::add(r1, j1);
+    v[4] = Cx<P>::sub(r1, j1);
+    v[2] = Cx<P>::add(r2, j2);
+    v[3] = Cx<P>::sub(r2, j2);
+  }
+};
+
+template <typename P, bool INV> struct Dft<P, 8, INV> {
+  using A = Ar<P>;
+  using C = typename A::C;
+  __device__ __forceinline__ static void run(C* v) {
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<P, 4, INV>::run(e);
+    Dft<P, 4, INV>::run(o);
+    // o_p *= exp(-+2 pi i p / 8): (1 -+ i)/sqrt2, -+i, (-1 -+ i)/sqrt2
+    {
+      const C t = Cx<P>::template mmi<INV>(o[1]);                 // -+i o1
+      o[1] = Cx<P>::mulk(Cx<P>::add(o[1], t), KR2);                // (1 -+ i) o1 / sqrt2
+    }
+    o[2] = Cx<P>::template mmi<INV>(o[2]);
+    {
+      const C t = Cx<P>::template mmi<INV>(o[3]);
+      o[3] = Cx<P>::mulk(Cx<P>::sub(t, o[3]), KR2);                // (-1 -+ i) o3 / sqrt2
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      v[p] = Cx<P>::add(e[p], o[p]);
+      v[p + 4] = Cx<P>::sub(e[p], o[p]);
+    }
+  }
+};
+
+// Shared-memory layout: the NP complex signals of a CTA are interleaved,
+// element t of signal p at t * NP + p, so one time step (or frequency) of all
+// the CTA's channels is contiguous, like a row of the HBM arrays.  16-byte
+// chunks are XOR-swizzled inside each 128-byte line (chunk ^= line mod 8):
+// the strided rows of a first radix pass then fall on distinct banks.
+template <typename C>
+__device__ __forceinline__ int swz(int e) {
+  if constexpr (sizeof(C) == 8) return e ^ ((e >> 3) & 14);
+  else return e ^ ((e >> 3) & 7);
+}
+template <typename C, int NP>
+__device__ __forceinline__ int sidx(int t, int p) { return swz<C>(t * NP + p); }
+
+// One Stockham pass of radix R over the CTA's NP signals of length L.
+// Butterfly j (< L/R) of signal p takes elements j + q L/R (q < R), applies the
+// twiddles exp(-+2 pi i q k / (Ns R)) of its position k = j mod Ns inside the
+// current sub-transform, and hands its R outputs to `dst` at (j - k) R + k + q Ns.
+// KMODE: 0 the first pass (Ns = 1, no twiddles), 1 a middle pass (k from a
+// multiply-high by the plan's magic constant), 2 the last pass (Ns = L/R, so
+// k = j).  A thread keeps all its butterflies (at most E / R, rounded up) in
+// registers, so with SYNC_MID the pass runs in place on one shared buffer:
+// every read, a barrier, then every write.  `src(t, p, e)` gets the input
+// position t = j + q L/R, the signal and the interleaved element index
+// e = t NP + p; `dst(t, p, e, v)` the same for an output.
+template <typename P, int R, bool INV, int NP, int E, int KMODE, bool SYNC_MID, class Src, class Dst>
+__device__ __forceinline__ void radix_pass(int T, int L, int Ns, int tws, unsigned magic,
+                                           const typename Ar<P>::C* __restrict__ tw, Src src, Dst dst) {
+  using A = Ar<P>;
+  using C = typename A::C;
+  constexpr int IT = (E + R - 1) / R;
+  const int nb = L / R, nbt = nb * NP;
+  C v[IT][R];
+#pragma unroll
+  for (int i = 0; i < IT; ++i) {
+    const int jt = threadIdx.x + i * T;
+    if (jt < nbt) {
+      const int j = jt / NP, p = jt % NP;
+#pragma unroll
+      for (int q = 0; q < R; ++q) v[i][q] = src(j + q * nb, p, jt + q * nbt);
+    }
+  }
+  if constexpr (SYNC_MID) __syncthreads();
+#pragma unroll
+  for (int i = 0; i < IT; ++i) {
+    const int jt = threadIdx.x + i * T;
+    if (jt < nbt) {
+      const int j = jt / NP, p = jt % NP;
+      int k = 0;
+      if constexpr (KMODE == 2) k = j;
+      else if constexpr (KMODE == 1) k = Ns > 1 ? j - (int)__umulhi((unsigned)j, magic) * Ns : 0;
+      if (KMODE != 0 && k > 0) {
+        const int kt = k * tws;
+#pragma unroll
+        for (int q = 1; q < R; ++q) {
+          C w = tw[q * kt];
+          if (INV) w = A::conj(w);
+          v[i][q] = A::cmul(v[i][q], w);
+        }
+      }
+      Dft<P, R, INV>::run(v[i]);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int t = base + q * Ns;
+        dst(t, p, t * NP + p, v[i][q]);
+      }
+    }
+  }
+}
+
+template <typename P, bool INV, int NP, int E, int KMODE, bool SYNC_MID, class Src, class Dst>
+__device__ __forceinline__ void any_pass(const FftPlan& plan, int ps, const typename Ar<P>::C* __restrict__ tw, Src src,
+                                         Dst dst) {
+  const int L = plan.L, Ns = plan.ns[ps], tws = plan.tws[ps];
+  const unsigned mg = plan.magic[ps];
+  switch (plan.rad[ps]) {
+    case 2: radix_pass<P, 2, INV, NP, E, KMODE, SYNC_MID>(blockDim.x, L, Ns, tws, mg, tw, src, dst); break;
+    case 3: radix_pass<P, 3, INV, NP, E, KMODE, SYNC_MID>(blockDim.x, L, Ns, tws, mg, tw, src, dst); break;
+    case 4: radix_pass<P, 4, INV, NP, E, KMODE, SYNC_MID>(blockDim.x, L, Ns, tws, mg, tw, src, dst); break;
+    case 5: radix_pass<P, 5, INV, NP, E, KMODE, SYNC_MID>(blockDim.x, L, Ns, tws, mg, tw, src, dst); break;
+    default: radix_pass<P, 8, INV, NP, E, KMODE, SYNC_MID>(blockDim.x, L, Ns, tws, mg, tw, src, dst); break;
+  }
+}
+
+// Passes [p0, p1) of the plan in place in shared memory, each followed by a
+// barrier.  make_plan groups the radices in the order 8, 4, 2, 5, 3; every
+// group runs in a loop of its own (one inlined pass body per loop keeps the
+// register allocation of each radix separate).
+template <typename P, bool INV, int NP, int E, class Src, class Dst>
+__device__ __forceinline__ void inplace_passes(const FftPlan& plan, int p0, int p1,
+                                               const typename Ar<P>::C* __restrict__ tw, Src src, Dst dst) {
+  int ps = p0;
+#define FFTMV_RADIX_LOOP(RR)                                                                          \
+  for (; ps < p1 && plan.rad[ps] == RR; ++ps) {                                                       \
+    radix_pass<P, RR, INV, NP, E, 1, true>(blockDim.x, plan.L, plan.ns[ps], plan.tws[ps], plan.magic[ps], tw, src, dst); \
+    __syncthreads();                                                                                  \
+  }
+  FFTMV_RADIX_LOOP(8)
+  FFTMV_RADIX_LOOP(4)
+  FFTMV_RADIX_LOOP(2)
+  FFTMV_RADIX_LOOP(5)
+  FFTMV_RADIX_LOOP(3)
+#undef FFTMV_RADIX_LOOP
+}
+
+// complex elements a thread holds during a pass: FP32 complexes take two
+// registers, FP64 and double-float ones four
+#ifndef FFTMV_FFT_E32
+#define FFTMV_FFT_E32 16
+#endif
+#ifndef FFTMV_FFT_E64
+#define FFTMV_FFT_E64 8
+#endif
+template <typename P> constexpr int kFftE = std::is_same<P, float>::value ? FFTMV_FFT_E32 : FFTMV_FFT_E64;
+
+// Channel pairs per CTA: the most (up to 8) whose signals fit in 64 KB, so
+// that two CTAs share an SM; threads: enough for E elements each.
+#ifndef FFTMV_FFT_TILE_KB
+#define FFTMV_FFT_TILE_KB 64
+#endif
+constexpr size_t kFftTileBytes = FFTMV_FFT_TILE_KB * 1024;
+template <typename P>
+__host__ __device__ constexpr int fft_pairs(int L) {
+  int np = 8;
+  while (np > 1 && (size_t)np * L * sizeof(typename Ar<P>::C) > kFftTileBytes) np /= 2;
+  return np;
+}
+template <typename P>
+__host__ __device__ constexpr int fft_nthreads(int np, int L) {
+  const int t = ((np * L + kFftE<P> - 1) / kFftE<P> + 31) / 32 * 32;
+  return t < 64 ? 64 : t;
+}
+
+// --- lengths known at compile time ------------------------------------------
+// The workloads' lengths get kernels of their own (FFTMV_FIXED_LENGTHS below):
+// with L constant the plan, the pass sequence, the thread count and every
+// index computation fold into constants.  Other lengths take the runtime plan.
+struct CPlan {
+  int npass;
+  int rad[kMaxPasses];
+  int ns[kMaxPasses];
+};
+// the same radix order as make_plan: 8, 4, 2, 5, 3
+__host__ __device__ constexpr CPlan cplan(int L) {
+  CPlan p{};
+  int n = L, np = 0;
+  const int order[5] = {8, 4, 2, 5, 3};
+  for (int o = 0; o < 5; ++o)
+    while (n % order[o] == 0) {
+      p.rad[np++] = order[o];
+      n /= order[o];
+    }
+  p.npass = np;
+  int ns = 1;
+  for (int i = 0; i < np; ++i) {
+    p.ns[i] = ns;
+    ns *= p.rad[i];
+  }
+  return p;
+}
+__host__ __device__ constexpr unsigned cmagic(int ns) {
+  return ns > 1 ? (unsigned)((((unsigned long long)1 << 32) + (unsigned long long)ns - 1) / (unsigned long long)ns) : 0u;
+}
+
+// pass PS of the length-L plan
+template <typename P, bool INV, int NP, int E, int L, int PS, int KMODE, bool SYNC_MID, class Src, class Dst>
+__device__ __forceinline__ void cpass(int T, const typename Ar<P>::C* __restrict__ tw, Src src, Dst dst) {
+  constexpr CPlan pl = cplan(L);
+  constexpr int R = pl.rad[PS], Ns = pl.ns[PS];
+  radix_pass<P, R, INV, NP, E, KMODE, SYNC_MID>(T, L, Ns, L / (Ns * R), cmagic(Ns), tw, src, dst);
+}
+// passes [PS, PE) in place, each followed by a barrier
+template <typename P, bool INV, int NP, int E, int L, int PS, int PE, class Src, class Dst>
+__device__ __forceinline__ void cpasses(int T, const typename Ar<P>::C* __restrict__ tw, Src src, Dst dst) {
+  if constexpr (PS < PE) {
+    cpass<P, INV, NP, E, L, PS, 1, true>(T, tw, src, dst);
+    __syncthreads();
+    cpasses<P, INV, NP, E, L, PS + 1, PE>(T, tw, src, dst);
+  }
+}
+
+// --- loads and stores with the phase casts --------------------------------
+
+template <typename P, typename Tin>
+__device__ __forceinline__ typename Ar<P>::R load_real(const void* p, int64_t i, bool pad_single) {
+  const Tin x = __ldg(static_cast<const Tin*>(p) + i);
+  if (pad_single) return Ar<P>::from_f((float)x);
+  if constexpr (sizeof(Tin) == 8) return Ar<P>::from_d((double)x);
+  else return Ar<P>::from_f((float)x);
+}
+
+// store one complex value (re, im) of precision P into format fmt
+template <typename P>
+__device__ __forceinline__ void store_cx(void* X, int64_t i, int fmt, typename Ar<P>::R re, typename Ar<P>::R im) {
+  using A = Ar<P>;
+  if (fmt == FMT_C128) {
+    static_cast<double2*>(X)[i] = make_double2(A::to_d(re), A::to_d(im));
+  } else if (fmt == FMT_C64) {
+    static_cast<float2*>(X)[i] = make_float2(A::to_f(re), A::to_f(im));
+  } else {
+    if constexpr (std::is_same<P, double>::value) {
+      // FP64 value -> hi/lo pair
+      const double r = A::to_d(re), m = A::to_d(im);
+      const float hr = (float)r, hm = (float)m;
+      static_cast<float4*>(X)[i] = make_float4(hr, hm, (float)(r - (double)hr), (float)(m - (double)hm));
+    } else if constexpr (std::is_same<P, DFP>::value) {
+      static_cast<float4*>(X)[i] = Ar<DFP>::mk(re, im);
+    } else {
+      static_cast<float4*>(X)[i] = make_float4(A::to_f(re), A::to_f(im), 0.f, 0.f);
+    }
+  }
+}
+
+// load one complex value stored in format fmt into precision P
+template <typename P>
+__device__ __forceinline__ typename Ar<P>::C load_cx(const void* X, int64_t i, int fmt) {
+  using A = Ar<P>;
+  if (fmt == FMT_C128) {
+    const double2 v = __ldg(static_cast<const double2*>(X) + i);
+    return A::mk(A::from_d(v.x), A::from_d(v.y));
+  }
+  if (fmt == FMT_C64) {
+    const float2 v = __ldg(static_cast<const float2*>(X) + i);
+    return A::mk(A::from_f(v.x), A::from_f(v.y));
+  }
+  const float4 v = __ldg(static_cast<const float4*>(X) + i);
+  if constexpr (std::is_same<P, DFP>::value) {
+    return v;
+  } else if constexpr (std::is_same<P, double>::value) {
+    return A::mk((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  } else {
+    return A::mk(__fadd_rn(v.x, v.z), __fadd_rn(v.y, v.w));
+  }
+}
+
+// Forward: pad + real FFT; grid (row x channel group, K).  A CTA owns NP
+// adjacent channel pairs (2 NP channels); pair p is the complex signal
+// x_{c0+2p} + i x_{c0+2p+1}.  The first radix pass reads the samples straight
+// from HBM (zero padding and the pad cast fused: t >= Nt is never read), the
+// other passes run in place in shared memory, then the real/imaginary split
+// writes the spectra.
+template <typename Tin, typename P, int NP, int LC>
+__global__ void __launch_bounds__(1024, 1) rfft_fwd_kernel(FwdDesc d) {
+  using A = Ar<P>;
+  using C = typename A::C;
+  using R = typename A::R;
+  constexpr int E = kFftE<P>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int L = LC > 0 ? LC : d.plan.L;
+  const int T = LC > 0 ? fft_nthreads<P>(NP, LC) : (int)blockDim.x;
+  const int Nf = L / 2 + 1;
+  constexpr int NCH = 2 * NP;
+  const int groups = (d.out_cols + NCH - 1) / NCH;
+  const int row = blockIdx.x / groups;
+  const int c0 = (blockIdx.x - row * groups) * NCH;
+  const int b = blockIdx.y;
+  const int64_t xo = b * d.x_ld_b + row * d.x_ld_row;
+  const C* tw = static_cast<const C*>(d.tw);
+  const C zero = A::mk(A::zero(), A::zero());
+
+  auto gsrc = [&](int t, int p, int) -> C {
+    const int c = c0 + 2 * p;
+    if (t >= d.Nt || c >= d.cols) return zero;
+    const int64_t o = xo + t * d.x_ld_t + c;
+    const R a = load_real<P, Tin>(d.x, o, d.pad_single);
+    const R bb = c + 1 < d.cols ? load_real<P, Tin>(d.x, o + 1, d.pad_single) : A::zero();
+    return A::mk(a, bb);
+  };
+  auto sdst = [&](int, int, int e, C v) { buf[swz<C>(e)] = v; };
+  auto ssrc = [&](int, int, int e) -> C { return buf[swz<C>(e)]; };
+  if constexpr (LC > 0) {
+    cpass<P, false, NP, E, LC, 0, 0, false>(T, tw, gsrc, sdst);
+    __syncthreads();
+    cpasses<P, false, NP, E, LC, 1, cplan(LC).npass>(T, tw, ssrc, sdst);
+  } else {
+    any_pass<P, false, NP, E, 0, false>(d.plan, 0, tw, gsrc, sdst);
+    __syncthreads();
+    inplace_passes<P, false, NP, E>(d.plan, 1, d.plan.npass, tw, ssrc, sdst);
+  }
+
+  // split: X_a = (Z_w + conj Z_{L-w}) / 2,  X_b = (Z_w - conj Z_{L-w}) / (2i)
+  auto split = [&](int w, int cc, R& xr, R& xi) {
+    const C z = buf[sidx<C, NP>(w, cc >> 1)];
+    const C zc = buf[sidx<C, NP>(w == 0 ? 0 : L - w, cc >> 1)];
+    if (cc & 1) {
+      xr = A::half(A::add(A::im(z), A::im(zc)));
+      xi = A::half(A::sub(A::re(zc), A::re(z)));
+    } else {
+      xr = A::half(A::add(A::re(z), A::re(zc)));
+      xi = A::half(A::sub(A::im(z), A::im(zc)));
+    }
+  };
+  if (d.fmt == FMT_TC) {
+    // bf16 hi/lo B planes [2][J][ldb/64][Nf][64] (ldb = out_cols): a thread
+    // takes one frequency and G adjacent channels, and writes them as one
+    // 2G-byte run into each of the four rows (Re, Im) x (hi, lo)
+    constexpr int G = NCH < 8 ? NCH : 8;
+    constexpr int NG = NCH / G;
+    using Vec = typename std::conditional<G == 8, uint4, typename std::conditional<G == 4, uint2, uint32_t>::type>::type;
+    __nv_bfloat16* B = static_cast<__nv_bfloat16*>(d.X);
+    const int ch = b / d.tc_KC, q = b - ch * d.tc_KC;
+    const int64_t jr = (int64_t)ch * d.tc_N + q, ji = jr + d.tc_KC;
+    const int64_t row_el = (int64_t)d.out_cols * Nf;   // bf16 per B row
+    const int64_t plane_el = (int64_t)d.tc_J * row_el;
+    for (int i = threadIdx.x; i < Nf * NG; i += T) {
+      const int w = i / NG, g = i % NG;
+      const int cg = g * G, c = c0 + cg;
+      if (c >= d.out_cols) continue;
+      __align__(16) __nv_bfloat16 h[4][G];   // rows: Re hi, Re lo, Im hi, Im lo
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        float fr = 0.f, fi = 0.f;
+        if (c + u < d.cols) {
+          R xr, xi;
+          split(w, cg + u, xr, xi);
+          fr = A::to_f(xr);
+          fi = A::to_f(xi);
+        }
+        h[0][u] = __float2bfloat16(fr);
+        h[1][u] = __float2bfloat16(fr - __bfloat162float(h[0][u]));
+        h[2][u] = __float2bfloat16(fi);
+        h[3][u] = __float2bfloat16(fi - __bfloat162float(h[2][u]));
+      }
+      const int64_t off = ((int64_t)(c >> 6) * Nf + w) * 64 + (c & 63);
+      *reinterpret_cast<Vec*>(B + jr * row_el + off) = *reinterpret_cast<const Vec*>(h[0]);
+      *reinterpret_cast<Vec*>(B + plane_el + jr * row_el + off) = *reinterpret_cast<const Vec*>(h[1]);
+      *reinterpret_cast<Vec*>(B + ji * row_el + off) = *reinterpret_cast<const Vec*>(h[2]);
+      *reinterpret_cast<Vec*>(B + plane_el + ji * row_el + off) = *reinterpret_cast<const Vec*>(h[3]);
+    }
+    return;
+  }
+  // frequency-major spectra X[b][w][row][col]: consecutive threads on consecutive channels
+  const int64_t Xo = b * d.X_ld_b + row * d.X_ld_row;
+  for (int i = threadIdx.x; i < Nf * NCH; i += T) {
+    const int w = i / NCH, cc = i - w * NCH;
+    const int c = c0 + cc;
+    if (c >= d.out_cols) continue;
+    R xr = A::zero(), xi = A::zero();
+    if (c < d.cols) split(w, cc, xr, xi);
+    store_cx<P>(d.X, Xo + w * d.X_ld_w + c, d.fmt, xr, xi);
+  }
+}
+
+template <typename Tout, typename P>
+__device__ __forceinline__ void store_real(void* y, int64_t i, typename Ar<P>::R v, bool unpad_single) {
+  if (unpad_single || sizeof(Tout) == 4) {
+    static_cast<Tout*>(y)[i] = (Tout)Ar<P>::to_f(v);
+  } else {
+    static_cast<Tout*>(y)[i] = (Tout)Ar<P>::to_d(v);
+  }
+}
+
+// Inverse: Hermitian assembly + inverse complex FFT + unpad; grid (channel group, K).
+// The assembly loads the half spectra into shared memory, the passes run in
+// place, and the last pass writes t < Nt straight to HBM (1/L scale, unpad and
+// output cast fused).
+template <typename P, typename Tout, int NP, int LC>
+__global__ void __launch_bounds__(1024, 1) irfft_inv_kernel(InvDesc d) {
+  using A = Ar<P>;
+  using C = typename A::C;
+  constexpr int E = kFftE<P>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int L = LC > 0 ? LC : d.plan.L;
+  const int T = LC > 0 ? fft_nthreads<P>(NP, LC) : (int)blockDim.x;
+  const int Nf = L / 2 + 1;
+  constexpr int NCH = 2 * NP;
+  const int c0 = blockIdx.x * NCH;
+  const int b = blockIdx.y;
+  const int64_t Xo = b * d.X_ld_b;
+  // Z_w = X_a(w) + i X_b(w) over the full circle, X(L-w) = conj X(w); the DC and
+  // Nyquist terms of a real signal's spectrum are taken as real.  Thread i
+  // reads channel pair i % NP at frequency i / NP (two adjacent entries).
+  constexpr int U = 4;   // loads in flight per thread
+  const C zero = A::mk(A::zero(), A::zero());
+  for (int i0 = threadIdx.x; i0 < Nf * NP; i0 += U * T) {
+    C a[U], bb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * T;
+      const int w = i / NP, p = i - w * NP;
+      const int ca = c0 + 2 * p, cb = ca + 1;
+      const bool in = i < Nf * NP;
+      a[u] = in && ca < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt) : zero;
+      bb[u] = in && cb < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * T;
+      if (i >= Nf * NP) break;
+      const int w = i / NP, p = i - w * NP;
+      if (w == 0 || w == Nf - 1) {
+        buf[sidx<C, NP>(w, p)] = A::mk(A::re(a[u]), A::re(bb[u]));
+      } else {
+        buf[sidx<C, NP>(w, p)] = A::mk(A::sub(A::re(a[u]), A::im(bb[u])), A::add(A::im(a[u]), A::re(bb[u])));
+        buf[sidx<C, NP>(L - w, p)] = A::mk(A::add(A::re(a[u]), A::im(bb[u])), A::sub(A::re(bb[u]), A::im(a[u])));
+      }
+    }
+  }
+  __syncthreads();
+  const C* tw = static_cast<const C*>(d.tw);
+  auto sdst = [&](int, int, int e, C v) { buf[swz<C>(e)] = v; };
+  auto ssrc = [&](int, int, int e) -> C { return buf[swz<C>(e)]; };
+  if constexpr (LC > 0) cpasses<P, true, NP, E, LC, 0, cplan(LC).npass - 1>(T, tw, ssrc, sdst);
+  else inplace_passes<P, true, NP, E>(d.plan, 0, d.plan.npass - 1, tw, ssrc, sdst);
+  const Kc inv_L{d.inv_L, d.inv_L_hi, d.inv_L_lo};
+  auto gdst = [&](int t, int p, int, C v) {
+    const int c = c0 + 2 * p;
+    if (t >= d.Nt || c >= d.cols) return;
+    const int64_t o = b * d.y_ld_b + t * d.y_ld_t + c;
+    store_real<Tout, P>(d.y, o, A::mulk(A::re(v), inv_L), d.unpad_single);
+    if (c + 1 < d.cols) store_real<Tout, P>(d.y, o + 1, A::mulk(A::im(v), inv_L), d.unpad_single);
+  };
+  if constexpr (LC > 0) cpass<P, true, NP, E, LC, cplan(LC).npass - 1, 2, false>(T, tw, ssrc, gdst);
+  else any_pass<P, true, NP, E, 2, false>(d.plan, d.plan.npass - 1, tw, ssrc, gdst);
+}
+
+template <typename K>
+cudaError_t prep(K kernel, size_t smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+
+template <typename Tin, typename P, int NP, int LC>
+cudaError_t fwd_launch_np(const FwdDesc& d, cudaStream_t s) {
+  const int groups = (d.out_cols + 2 * NP - 1) / (2 * NP);
+  dim3 grid(d.rows * groups, d.K);
+  const size_t smem = (size_t)NP * d.plan.L * sizeof(typename Ar<P>::C);
+  const int threads = fft_nthreads<P>(NP, d.plan.L);
+  if (threads > 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = prep(rfft_fwd_kernel<Tin, P, NP, LC>, smem);
+  if (e != cudaSuccess) return e;
+  rfft_fwd_kernel<Tin, P, NP, LC><<<grid, threads, smem, s>>>(d);
+  return cudaGetLastError();
+}
+
+template <typename P, typename Tout, int NP, int LC>
+cudaError_t inv_launch_np(const InvDesc& d, cudaStream_t s) {
+  dim3 grid((d.cols + 2 * NP - 1) / (2 * NP), d.K);
+  const size_t smem = (size_t)NP * d.plan.L * sizeof(typename Ar<P>::C);
+  const int threads = fft_nthreads<P>(NP, d.plan.L);
+  if (threads > 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = prep(irfft_inv_kernel<P, Tout, NP, LC>, smem);
+  if (e != cudaSuccess) return e;
+  irfft_inv_kernel<P, Tout, NP, LC><<<grid, threads, smem, s>>>(d);
+  return cudaGetLastError();
+}
+
+// the lengths with kernels of their own: L = 2 Nt for Nt = 64, 128, 256, 500, 1000
+#define FFTMV_FIXED_LENGTHS(X) X(128) X(256) X(512) X(1000) X(2000)
+
+template <typename Tin, typename P>
+cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
+  switch (d.plan.L) {
+#define FFTMV_CASE(LL) \
+  case LL: return fwd_launch_np<Tin, P, fft_pairs<P>(LL), LL>(d, s);
+    FFTMV_FIXED_LENGTHS(FFTMV_CASE)
+#undef FFTMV_CASE
+    default: break;
+  }
+  switch (fft_pairs<P>(d.plan.L)) {
+    case 8: return fwd_launch_np<Tin, P, 8, 0>(d, s);
+    case 4: return fwd_launch_np<Tin, P, 4, 0>(d, s);
+    case 2: return fwd_launch_np<Tin, P, 2, 0>(d, s);
+    default: return fwd_launch_np<Tin, P, 1, 0>(d, s);
+  }
+}
+
+template <typename P, typename Tout>
+cudaError_t inv_launch(const InvDesc& d, cudaStream_t s) {
+  switch (d.plan.L) {
+#define FFTMV_CASE(LL) \
+  case LL: return inv_launch_np<P, Tout, fft_pairs<P>(LL), LL>(d, s);
+    FFTMV_FIXED_LENGTHS(FFTMV_CASE)
+#undef FFTMV_CASE
+    default: break;
+  }
+  switch (fft_pairs<P>(d.plan.L)) {
+    case 8: return inv_launch_np<P, Tout, 8, 0>(d, s);
+    case 4: return inv_launch_np<P, Tout, 4, 0>(d, s);
+    case 2: return inv_launch_np<P, Tout, 2, 0>(d, s);
+    default: return inv_launch_np<P, Tout, 1, 0>(d, s);
+  }
+}
+
+}  // namespace
+}  // namespace fftmv

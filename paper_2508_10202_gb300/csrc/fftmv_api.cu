@@ -73,6 +73,13 @@ FftPlan make_plan(int64_t L) {
   while (n % 5 == 0) { p.rad[np++] = 5; n /= 5; }
   while (n % 3 == 0) { p.rad[np++] = 3; n /= 3; }
   p.npass = np;
+  int64_t ns = 1;
+  for (int i = 0; i < np; ++i) {
+    p.ns[i] = (int)ns;
+    p.tws[i] = (int)(L / (ns * p.rad[i]));
+    p.magic[i] = ns > 1 ? (unsigned)(((uint64_t)1 << 32) / (uint64_t)ns + (((uint64_t)1 << 32) % (uint64_t)ns != 0)) : 0u;
+    ns *= p.rad[i];
+  }
   return p;
 }
 
@@ -204,10 +211,9 @@ CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
   c.Cout = fwd ? op->Nd : op->Nm;
   c.in_ld = fwd ? op->ldn : op->Nd;
   c.out_ld = fwd ? op->Nd : op->ldn;
-  if (c.kind == GEMV_TC) {  // B operand planes [Nf][2][J][ld] bf16, then the channel-major spectra
-    if (!fwd) c.in_ld = (op->Nd + 7) / 8 * 8;   // d-hat channels padded like the rows of F-hat
-    c.in_hat = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld)) +
-               align256(tc_spectrum_bytes((int)K, (int)op->Nf, (int)c.in_ld));
+  if (c.kind == GEMV_TC) {  // B operand planes [2][J][ldb/64][Nf][64] bf16
+    c.in_ld = tc_ldb((int)c.Cin);
+    c.in_hat = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld));
   } else {
     c.in_hat = align256((size_t)K * op->Nf * c.in_ld * fmt_bytes(c.in_fmt));
   }
@@ -243,17 +249,16 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   f.fmt = c.in_fmt;
   f.pad_single = p.pad == FFTMV_F32;
   cudaError_t e = cudaSuccess;
-  void* tc_T = nullptr;
   if (c.kind == GEMV_TC) {
     const TcShape t = tc_shape((int)K);
-    const size_t bbytes = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld));
-    tc_T = static_cast<char*>(in_hat) + bbytes;
-    f.X = tc_T;
+    f.tc_KC = t.KC;
+    f.tc_N = t.N;
+    f.tc_J = t.J;
     // B rows no right-hand side fills (chunk padding, a short last chunk) must read as zero
-    if (2 * t.KC < t.N || (int)K % t.KC != 0) e = cudaMemsetAsync(in_hat, 0, bbytes, s);
+    if (2 * t.KC < t.N || (int)K % t.KC != 0)
+      e = cudaMemsetAsync(in_hat, 0, tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld), s);
   }
   if (e == cudaSuccess) e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fprec, s);
-  if (e == cudaSuccess && tc_T) e = launch_tc_pack(tc_T, in_hat, (int)K, (int)op->Nf, (int)c.in_ld, s);
   if (ev) cudaEventRecord(ev[1], s);
   if (e == cudaSuccess) {
     GemvDesc g{};
@@ -276,7 +281,7 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
       t.Nd = (int)op->Nd;
       t.Nm = (int)op->Nm;
       t.ldn = (int)op->ldn;
-      t.ldr = (int)((op->Nd + 7) / 8 * 8);
+      t.ldb = (int)c.in_ld;
       t.K = (int)K;
       t.adjoint = !fwd;
       t.y_ld_b = op->Nf * c.out_ld;

@@ -13,8 +13,8 @@ enum CFmt : int {
   FMT_C128 = 0,  // double2 (re, im)
   FMT_C64 = 1,   // float2 (re, im)
   FMT_DF = 2,    // float4 (re_hi, im_hi, re_lo, im_lo): value = hi + lo, |lo| <= ulp(hi)/2
-  FMT_TC = 3,    // spectra for the tensor cores: channel-major float2 T[K][ldn][Nf], packed
-                 // afterwards into the bf16 B operand planes [Nf][hi, lo][J][ldn] (TcShape)
+  FMT_TC = 3,    // spectra for the tensor cores, written straight into the bf16 B operand
+                 // planes [hi, lo][J][ldb / 64][Nf][64] (TcShape, TcDesc)
 };
 
 // Arithmetic used by the per-frequency block matvec (phase 3).
@@ -35,10 +35,15 @@ enum FftPrec : int {
 constexpr int kMaxPasses = 16;
 
 // A mixed-radix (2, 3, 4, 5, 8) complex FFT of length L done in shared memory.
+// The passes are grouped by radix in the order 8, 4, 2, 5, 3 (the kernels rely
+// on it).
 struct FftPlan {
   int L;
   int npass;
   int rad[kMaxPasses];
+  int ns[kMaxPasses];         // sub-transform length before pass p (product of the earlier radices)
+  int tws[kMaxPasses];        // twiddle table stride L / (ns * rad)
+  unsigned magic[kMaxPasses]; // ceil(2^32 / ns): j / ns = umulhi(j, magic) for j < 2^16 (ns > 1)
 };
 
 // Forward real FFT of zero-padded channels (phases 1-2 fused).
@@ -58,6 +63,7 @@ struct FwdDesc {
   int64_t X_ld_w, X_ld_row, X_ld_b;     // complex-element strides of X
   int fmt;                 // CFmt of X
   int pad_single;          // round the loaded input to FP32 (pad phase in FP32)
+  int tc_KC, tc_N, tc_J;   // FMT_TC: right-hand sides per chunk, rows per chunk, rows per plane
 };
 
 // Inverse real FFT of Hermitian half spectra followed by unpad (phases 4-5 fused).
@@ -101,18 +107,18 @@ TcShape tc_shape(int K);
 
 struct TcDesc {
   const void* A;           // bf16 planes [Nf][4][Nd][ldn] (Re hi, Re lo, Im hi, Im lo)
-  const void* B;           // bf16 planes [Nf][2][J][ldk], ldk = ldn (F) or ldr (F*)
+  const void* B;           // bf16 planes [2][J][ldb / 64][Nf][64]: entry (plane, row j, frequency w,
+                           // contraction index k) at (((plane J + j) ldb/64 + k/64) Nf + w) 64 + k%64;
+                           // k < ldb = the contraction length (Nm for F, Nd for F*) rounded up to 64
   void* y;                 // FMT_C64 [K][Nf][Nd] (F) or [K][Nf][ldn] (F*)
-  int Nf, Nd, Nm, ldn, ldr, K;
+  int Nf, Nd, Nm, ldn, ldb, K;
   int adjoint;             // 0: F (contract over n), 1: F* (contract over r, A read transposed)
   int64_t y_ld_b;
   unsigned int* status;
 };
 cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s);
-// T[K][ldn][Nf] float2 -> B planes [Nf][2][J][ldn] bf16 (hi, lo) for K right-hand sides
-cudaError_t launch_tc_pack(const void* T, void* B, int K, int Nf, int ldn, cudaStream_t s);
-size_t tc_operand_bytes(int K, int Nf, int ldn);   // B planes
-size_t tc_spectrum_bytes(int K, int Nf, int ldn);  // T
+size_t tc_operand_bytes(int K, int Nf, int ldb);   // B planes
+int tc_ldb(int n);                                   // n rounded up to the 64-wide K block
 cudaError_t launch_convert_bf16x2(const double2* master, void* out, int Nf, int Nd, int ldn, cudaStream_t s);
 size_t tc_smem_bytes(int N);
 

@@ -57,6 +57,15 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -205,7 +214,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tma_load_4d(st + p * a_plane, &mapA, kb * TC_BK, m0, p, w, &full[s]);
           }
         }
-        for (int p = 0; p < 2; ++p) tma_load_4d(st + 4 * a_plane + p * b_plane, &mapB, kb * TC_BK, ch * N, p, w, &full[s]);
+        for (int p = 0; p < 2; ++p) tma_load_5d(st + 4 * a_plane + p * b_plane, &mapB, 0, w, kb, ch * N, p, &full[s]);
       }
       for (int kk = max(0, kb - TC_STAGES); kk < kb; ++kk)
         if (!mbar_wait(&full[kk % TC_STAGES], (kk / TC_STAGES) & 1)) ok = false;
@@ -318,46 +327,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-// Channel-major spectra T[b][n][w] (the FFT's natural order) -> tensor-core B
-// planes [w][hi, lo][row][n] through a 64-channel x 32-frequency shared-memory
-// tile: reads cover 32 consecutive frequencies of a channel, writes 64
-// consecutive channels (128 bytes of bf16) of one B row.
-constexpr int PK_N = 64, PK_W = 32;
-__global__ void __launch_bounds__(256) tc_pack_kernel(const float2* __restrict__ T, __nv_bfloat16* __restrict__ B,
-                                                      int K, int Nf, int ldn, int KC, int N, int J) {
-  __shared__ float2 tile[PK_N][PK_W + 1];
-  const int n0 = blockIdx.x * PK_N, w0 = blockIdx.y * PK_W, b = blockIdx.z;
-  const float2* src = T + (int64_t)b * ldn * Nf;
-  for (int i = threadIdx.x; i < PK_N * PK_W; i += 256) {
-    const int nn = i / PK_W, ww = i - nn * PK_W;
-    const int n = n0 + nn, w = w0 + ww;
-    tile[nn][ww] = (n < ldn && w < Nf) ? src[(int64_t)n * Nf + w] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  const int ch = b / KC, q = b - ch * KC;
-  const int jr = ch * N + q, ji = jr + KC;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n = n0 + 2 * lane;
-  for (int sgm = warp; sgm < PK_W * 4; sgm += 8) {   // (frequency, row type) segments
-    const int ww = sgm / 4, rt = sgm % 4;
-    const int w = w0 + ww;
-    if (w >= Nf || n >= ldn) continue;
-    const float2 a = tile[2 * lane][ww], c = tile[2 * lane + 1][ww];
-    const float va = rt < 2 ? a.x : a.y, vc = rt < 2 ? c.x : c.y;   // Re rows, then Im rows
-    const __nv_bfloat16 ha = __float2bfloat16(va), hc = __float2bfloat16(vc);
-    __nv_bfloat162 out;
-    if (rt % 2 == 0) {
-      out.x = ha;
-      out.y = hc;
-    } else {
-      out.x = __float2bfloat16(va - __bfloat162float(ha));
-      out.y = __float2bfloat16(vc - __bfloat162float(hc));
-    }
-    const int row = rt < 2 ? jr : ji, plane = rt % 2;
-    *reinterpret_cast<__nv_bfloat162*>(B + (((int64_t)w * 2 + plane) * J + row) * ldn + n) = out;
-  }
-}
-
 // master FP64 F-hat [Nf][Nd][ldn] -> four bf16 planes [Nf][4][Nd][ldn]: Re hi, Re lo, Im hi, Im lo
 __global__ void convert_bf16x2_kernel(const double2* __restrict__ in, __nv_bfloat16* __restrict__ out, int Nd, int ldn,
                                       int64_t n) {
@@ -401,6 +370,23 @@ cudaError_t make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// B operand map over bf16 planes [2][J][ldb / 64][Nf][64] (see TcDesc): dims
+// {64, Nf, ldb / 64, J, 2}, box {64, 1, 1, N, 1}.  The box lands in shared
+// memory as N rows of 64 contraction indices (128 bytes): the same K-major
+// 128-byte-swizzled tile a {64, N} box of a row-major plane gives.
+cudaError_t make_map_b(CUtensorMap* map, const void* base, uint64_t ldb, uint64_t J, uint64_t Nf, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[5] = {64, Nf, ldb / 64, J, 2};
+  const cuuint64_t strides[4] = {128, Nf * 128, ldb * Nf * 2, J * ldb * Nf * 2};
+  const cuuint32_t box[5] = {TC_BK, 1, 1, box_rows, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 TcShape tc_shape(int K) {
@@ -427,27 +413,17 @@ cudaError_t launch_convert_bf16x2(const double2* master, void* out, int Nf, int 
   return cudaGetLastError();
 }
 
-size_t tc_operand_bytes(int K, int Nf, int ldn) { return (size_t)Nf * 2 * tc_shape(K).J * ldn * 2; }
-size_t tc_spectrum_bytes(int K, int Nf, int ldn) { return (size_t)K * ldn * Nf * sizeof(float2); }
-
-cudaError_t launch_tc_pack(const void* T, void* B, int K, int Nf, int ldn, cudaStream_t s) {
-  if (K == 0) return cudaSuccess;
-  const TcShape t = tc_shape(K);
-  dim3 grid((ldn + PK_N - 1) / PK_N, (Nf + PK_W - 1) / PK_W, K);
-  tc_pack_kernel<<<grid, 256, 0, s>>>(static_cast<const float2*>(T), static_cast<__nv_bfloat16*>(B), K, Nf, ldn, t.KC,
-                                      t.N, t.J);
-  return cudaGetLastError();
-}
-
+size_t tc_operand_bytes(int K, int Nf, int ldb) { return (size_t)Nf * 2 * tc_shape(K).J * ldb * 2; }
+int tc_ldb(int n) { return (n + TC_BK - 1) / TC_BK * TC_BK; }
 cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s) {
   if (d.Nf == 0 || d.K == 0) return cudaSuccess;
   const TcShape t = tc_shape(d.K);
   const bool H = d.adjoint != 0;
-  const int ldk = H ? d.ldr : d.ldn;   // contraction length (padded) of the B operand
+  if (d.ldb % TC_BK != 0) return cudaErrorInvalidValue;
   CUtensorMap mapA, mapB;
   cudaError_t e = make_map(&mapA, d.A, (uint64_t)d.ldn, (uint64_t)d.Nd, 4, (uint64_t)d.Nf, H ? 64 : TC_M);
   if (e != cudaSuccess) return e;
-  e = make_map(&mapB, d.B, (uint64_t)ldk, (uint64_t)t.J, 2, (uint64_t)d.Nf, (uint32_t)t.N);
+  e = make_map_b(&mapB, d.B, (uint64_t)d.ldb, (uint64_t)t.J, (uint64_t)d.Nf, (uint32_t)t.N);
   if (e != cudaSuccess) return e;
   TcArgs a{};
   a.Nf = d.Nf;
@@ -455,7 +431,7 @@ cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s) {
   a.K = d.K;
   a.KC = t.KC;
   a.N = t.N;
-  a.nkb = H ? (d.Nd + TC_BK - 1) / TC_BK : (d.ldn + TC_BK - 1) / TC_BK;
+  a.nkb = d.ldb / TC_BK;
   a.y_ld_b = d.y_ld_b;
   a.y_ld_w = H ? d.ldn : d.Nd;
   a.y = static_cast<float2*>(d.y);
