@@ -146,11 +146,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 struct TcArgs {
   int Nf, M, K, KC, N, nkb;  // M: output rows (Nd for F, Nm for F*)
+  int nch, nmt;              // right-hand-side chunks and 128-row M tiles per frequency
   int64_t y_ld_b, y_ld_w;    // complex elements between right-hand sides / frequencies of y
   float2* y;                 // [K][Nf][rows] (FMT_C64)
   unsigned int* status;
 };
 
+// Persistent: each CTA loops over tiles (M tile, chunk, frequency), M tile
+// fastest, so the CTAs working at one time share a frequency's B operand in
+// L2.  Global k-block and group counters carry the pipeline phases across
+// tiles: the producer runs ahead into the next tile while the epilogue drains
+// the previous one from the other TMEM accumulator set.
 // H = false: F, A = F-hat_w (rows r, K along n, K-major).
 // H = true:  F*, A = F-hat_w^T (rows n, K along r, MN-major: the same planes read
 //            transposed); the conjugate enters through the epilogue signs.
@@ -171,9 +177,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* drained = ready + 2;           // [2]: epilogue has read the set
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 2);
 
-  const int w = blockIdx.x, ch = blockIdx.y, m0 = blockIdx.z * TC_M;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int ngroups = (a.nkb + TC_GROUP - 1) / TC_GROUP;
+  const int ntiles = a.Nf * a.nch * a.nmt;
+  const int gpt = (a.nkb + TC_GROUP - 1) / TC_GROUP;   // accumulation groups per tile
+  auto decode = [&](int tile, int& w, int& ch, int& m0) {
+    const int mt = tile % a.nmt, rest = tile / a.nmt;
+    ch = rest % a.nch;
+    w = rest / a.nch;
+    m0 = mt * TC_M;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -197,123 +209,138 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {  // TMA producer
-      int kb = 0;
-      for (; kb < a.nkb; ++kb) {
-        const int s = kb % TC_STAGES;
-        if (kb >= TC_STAGES && !mbar_wait(&empty[s], ((kb / TC_STAGES) & 1) ^ 1)) {
-          ok = false;
-          break;
-        }
-        unsigned char* st = tiles + s * stage_bytes;
-        mbar_arrive_expect_tx(&full[s], stage_bytes);
-        for (int p = 0; p < 4; ++p) {
-          if constexpr (H) {  // two 64 (n) x 64 (r) boxes per plane
-            tma_load_4d(st + p * a_plane, &mapA, m0, kb * TC_BK, p, w, &full[s]);
-            tma_load_4d(st + p * a_plane + a_plane / 2, &mapA, m0 + 64, kb * TC_BK, p, w, &full[s]);
-          } else {
-            tma_load_4d(st + p * a_plane, &mapA, kb * TC_BK, m0, p, w, &full[s]);
+      uint32_t it = 0;  // k-blocks issued by this CTA
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int w, ch, m0;
+        decode(tile, w, ch, m0);
+        for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+          const uint32_t s = it % TC_STAGES;
+          if (it >= TC_STAGES && !mbar_wait(&empty[s], ((it / TC_STAGES) & 1) ^ 1)) {
+            ok = false;
+            break;
           }
+          unsigned char* st = tiles + s * stage_bytes;
+          mbar_arrive_expect_tx(&full[s], stage_bytes);
+          for (int p = 0; p < 4; ++p) {
+            if constexpr (H) {  // two 64 (n) x 64 (r) boxes per plane
+              tma_load_4d(st + p * a_plane, &mapA, m0, kb * TC_BK, p, w, &full[s]);
+              tma_load_4d(st + p * a_plane + a_plane / 2, &mapA, m0 + 64, kb * TC_BK, p, w, &full[s]);
+            } else {
+              tma_load_4d(st + p * a_plane, &mapA, kb * TC_BK, m0, p, w, &full[s]);
+            }
+          }
+          for (int p = 0; p < 2; ++p) tma_load_5d(st + 4 * a_plane + p * b_plane, &mapB, 0, w, kb, ch * N, p, &full[s]);
         }
-        for (int p = 0; p < 2; ++p) tma_load_5d(st + 4 * a_plane + p * b_plane, &mapB, 0, w, kb, ch * N, p, &full[s]);
       }
-      for (int kk = max(0, kb - TC_STAGES); kk < kb; ++kk)
+      // no copy may still be in flight when the CTA exits
+      for (uint32_t kk = it > TC_STAGES ? it - TC_STAGES : 0; kk < it; ++kk)
         if (!mbar_wait(&full[kk % TC_STAGES], (kk / TC_STAGES) & 1)) ok = false;
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       const uint32_t idesc = umma_idesc_bf16(N) | (H ? (1u << 15) : 0u);   // bit 15: A is MN-major
-      for (int kb = 0; kb < a.nkb && ok; ++kb) {
-        const int g = kb / TC_GROUP, set = g & 1;
-        const bool first = kb % TC_GROUP == 0;
-        // the set was last used by group g-2: wait until the epilogue has read it
-        if (first && g >= 2 && !mbar_wait(&drained[set], ((g >> 1) - 1) & 1)) {
-          ok = false;
-          break;
-        }
-        const int s = kb % TC_STAGES;
-        if (!mbar_wait(&full[s], (kb / TC_STAGES) & 1)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t acc1 = tmem + 256 * set, acc2 = acc1 + 128;
-        unsigned char* st = tiles + s * stage_bytes;
+      uint32_t it = 0, G = 0;   // k-blocks consumed, groups started
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+          const bool first = kb % TC_GROUP == 0;
+          const uint32_t set = G & 1;
+          // the set was last used by group G-2: wait until the epilogue has read it
+          if (first && G >= 2 && !mbar_wait(&drained[set], ((G >> 1) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          const uint32_t s = it % TC_STAGES;
+          if (!mbar_wait(&full[s], (it / TC_STAGES) & 1)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t acc1 = tmem + 256 * set, acc2 = acc1 + 128;
+          unsigned char* st = tiles + s * stage_bytes;
 #pragma unroll
-        for (int ks = 0; ks < TC_BK / 16; ++ks) {
-          // +32 bytes per 16 bf16 along K inside the swizzled row: +2 in the address field
-          // A: K-major advances 32 B per 16 K inside the swizzled row; MN-major
-          // advances two 8-row K groups (2048 B)
-          const uint64_t ak = H ? (uint64_t)(2048 >> 4) * ks : 2 * ks;
-          const uint64_t frh = (H ? umma_desc_mn_sw128(st + 0 * a_plane) : umma_desc_sw128(st + 0 * a_plane)) + ak;
-          const uint64_t frl = (H ? umma_desc_mn_sw128(st + 1 * a_plane) : umma_desc_sw128(st + 1 * a_plane)) + ak;
-          const uint64_t fih = (H ? umma_desc_mn_sw128(st + 2 * a_plane) : umma_desc_sw128(st + 2 * a_plane)) + ak;
-          const uint64_t fil = (H ? umma_desc_mn_sw128(st + 3 * a_plane) : umma_desc_sw128(st + 3 * a_plane)) + ak;
-          const uint64_t bh = umma_desc_sw128(st + 4 * a_plane) + 2 * ks;
-          const uint64_t bl = umma_desc_sw128(st + 4 * a_plane + b_plane) + 2 * ks;
-          const uint32_t acc = !(first && ks == 0);
-          umma_bf16(acc1, frh, bh, idesc, acc);
-          umma_bf16(acc1, frh, bl, idesc, 1);
-          umma_bf16(acc1, frl, bh, idesc, 1);
-          umma_bf16(acc2, fih, bh, idesc, acc);
-          umma_bf16(acc2, fih, bl, idesc, 1);
-          umma_bf16(acc2, fil, bh, idesc, 1);
+          for (int ks = 0; ks < TC_BK / 16; ++ks) {
+            // A: K-major advances 32 B per 16 K inside the swizzled row; MN-major
+            // advances two 8-row K groups (2048 B).  B: K-major.
+            const uint64_t ak = H ? (uint64_t)(2048 >> 4) * ks : 2 * ks;
+            const uint64_t frh = (H ? umma_desc_mn_sw128(st + 0 * a_plane) : umma_desc_sw128(st + 0 * a_plane)) + ak;
+            const uint64_t frl = (H ? umma_desc_mn_sw128(st + 1 * a_plane) : umma_desc_sw128(st + 1 * a_plane)) + ak;
+            const uint64_t fih = (H ? umma_desc_mn_sw128(st + 2 * a_plane) : umma_desc_sw128(st + 2 * a_plane)) + ak;
+            const uint64_t fil = (H ? umma_desc_mn_sw128(st + 3 * a_plane) : umma_desc_sw128(st + 3 * a_plane)) + ak;
+            const uint64_t bh = umma_desc_sw128(st + 4 * a_plane) + 2 * ks;
+            const uint64_t bl = umma_desc_sw128(st + 4 * a_plane + b_plane) + 2 * ks;
+            const uint32_t acc = !(first && ks == 0);
+            umma_bf16(acc1, frh, bh, idesc, acc);
+            umma_bf16(acc1, frh, bl, idesc, 1);
+            umma_bf16(acc1, frl, bh, idesc, 1);
+            umma_bf16(acc2, fih, bh, idesc, acc);
+            umma_bf16(acc2, fih, bl, idesc, 1);
+            umma_bf16(acc2, fil, bh, idesc, 1);
+          }
+          umma_commit(&empty[s]);                                 // stage reusable
+          if (kb % TC_GROUP == TC_GROUP - 1 || kb == a.nkb - 1) {  // group done
+            umma_commit(&ready[set]);
+            ++G;
+          }
         }
-        umma_commit(&empty[s]);                                         // stage reusable
-        if (kb % TC_GROUP == TC_GROUP - 1 || kb == a.nkb - 1) umma_commit(&ready[set]);  // group done
       }
     }
   } else {  // epilogue: warps 2..9; TMEM lane quadrant warp % 4, half of the RHS columns each
     const int ew = warp - 2;
-    const int row = m0 + 32 * (warp % 4) + lane;
     const uint32_t lane_addr = (uint32_t)(32 * (warp % 4)) << 16;
     const int KC = a.KC, hw = (KC + 1) / 2;
     const int qlo = (ew / 4) * hw, qn = min(hw, KC - qlo);   // this warp's RHS columns [qlo, qlo + qn)
-    float sre[32], sim[32];
+    uint32_t G = 0;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      int w, ch, m0;
+      decode(tile, w, ch, m0);
+      const int row = m0 + 32 * (warp % 4) + lane;
+      float sre[32], sim[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) sre[i] = sim[i] = 0.f;
-    for (int g = 0; g < ngroups; ++g) {
-      const int set = g & 1;
-      bool got = mbar_wait(&ready[set], (g >> 1) & 1);
-      if (!__all_sync(0xffffffffu, got)) {  // tcgen05.ld is warp-collective
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t t1 = tmem + lane_addr + 256 * set, t2 = t1 + 128;
+      for (int i = 0; i < 32; ++i) sre[i] = sim[i] = 0.f;
+      for (int g = 0; g < gpt; ++g, ++G) {
+        const uint32_t set = G & 1;
+        const bool got = mbar_wait(&ready[set], (G >> 1) & 1);
+        if (!__all_sync(0xffffffffu, got)) {  // tcgen05.ld is warp-collective
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t t1 = tmem + lane_addr + 256 * set, t2 = t1 + 128;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        if (c * 16 < qn) {
-          float a1r[16], a1i[16], a2r[16], a2i[16];
-          const int q0 = qlo + c * 16;
-          tmem_ld16(t1 + q0, a1r);        // Re F * Re M
-          tmem_ld16(t1 + KC + q0, a1i);   // Re F * Im M
-          tmem_ld16(t2 + q0, a2r);        // Im F * Re M
-          tmem_ld16(t2 + KC + q0, a2i);   // Im F * Im M
+        for (int c = 0; c < 2; ++c) {
+          if (c * 16 < qn) {
+            float a1r[16], a1i[16], a2r[16], a2i[16];
+            const int q0 = qlo + c * 16;
+            tmem_ld16(t1 + q0, a1r);        // Re F * Re X
+            tmem_ld16(t1 + KC + q0, a1i);   // Re F * Im X
+            tmem_ld16(t2 + q0, a2r);        // Im F * Re X
+            tmem_ld16(t2 + KC + q0, a2i);   // Im F * Im X
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            if constexpr (H) {  // conj(F) M: Re = ReF ReM + ImF ImM, Im = ReF ImM - ImF ReM
-              sre[c * 16 + i] += a1r[i] + a2i[i];
-              sim[c * 16 + i] += a1i[i] - a2r[i];
-            } else {
-              sre[c * 16 + i] += a1r[i] - a2i[i];
-              sim[c * 16 + i] += a1i[i] + a2r[i];
+            for (int i = 0; i < 16; ++i) {
+              if constexpr (H) {  // conj(F) X: Re = ReF ReX + ImF ImX, Im = ReF ImX - ImF ReX
+                sre[c * 16 + i] += a1r[i] + a2i[i];
+                sim[c * 16 + i] += a1i[i] - a2r[i];
+              } else {
+                sre[c * 16 + i] += a1r[i] - a2i[i];
+                sim[c * 16 + i] += a1i[i] + a2r[i];
+              }
             }
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&drained[set]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&drained[set]);
-    }
-    if (ok && row < a.M) {
+      if (ok && row < a.M) {
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < 2; ++c) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int q = qlo + c * 16 + i;
-          const int b = ch * KC + q;
-          if (c * 16 + i < qn && b < a.K)
-            a.y[b * a.y_ld_b + (int64_t)w * a.y_ld_w + row] = make_float2(sre[c * 16 + i], sim[c * 16 + i]);
+          for (int i = 0; i < 16; ++i) {
+            const int q = qlo + c * 16 + i;
+            const int b = ch * KC + q;
+            if (c * 16 + i < qn && b < a.K)
+              a.y[b * a.y_ld_b + (int64_t)w * a.y_ld_w + row] = make_float2(sre[c * 16 + i], sim[c * 16 + i]);
+          }
         }
       }
     }
@@ -432,6 +459,8 @@ cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s) {
   a.KC = t.KC;
   a.N = t.N;
   a.nkb = d.ldb / TC_BK;
+  a.nch = t.nch;
+  a.nmt = (a.M + TC_M - 1) / TC_M;
   a.y_ld_b = d.y_ld_b;
   a.y_ld_w = H ? d.ldn : d.Nd;
   a.y = static_cast<float2*>(d.y);
@@ -440,7 +469,12 @@ cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s) {
   auto kernel = H ? tc_gemm_kernel<true> : tc_gemm_kernel<false>;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(d.Nf, t.nch, (a.M + TC_M - 1) / TC_M);
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (int64_t)d.Nf * t.nch * a.nmt;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);   // one persistent CTA per SM
   kernel<<<grid, TC_THREADS, smem, s>>>(mapA, mapB, a);
   return cudaGetLastError();
 }
