@@ -177,35 +177,40 @@ struct KindF32 {
 };
 
 // ---------------------------------------------------------------------------
-// N direction: grid (ceil(Nd / R), Nf, K).  Warp-specialised bulk-copy pipeline:
-// warp 0 (one elected thread) streams each CW-pack segment of the R rows of
-// F-hat_w and the matching segment of m-hat_w into a ring of STAGES shared
-// memory stages with cp.async.bulk, completion counted on the stage's "full"
-// mbarrier; NCW consumer warps compute from shared memory (consumer thread tc
-// owns pack tc of every segment, so its columns are tc, tc + CW, ...) and
-// release the stage through its "empty" mbarrier.  Bytes stay in flight while
-// the consumers do their double-float arithmetic.
+// N direction: grid (ceil(Nd / R), Nf, ceil(K / KB)).  Warp-specialised
+// bulk-copy pipeline: warp 0 (one elected thread) streams each CW-pack segment
+// of the R rows of F-hat_w and the matching segments of KB right-hand sides
+// m-hat_w into a ring of STAGES shared-memory stages with cp.async.bulk,
+// completion counted on the stage's "full" mbarrier; NCW consumer warps
+// compute from shared memory (consumer thread tc owns pack tc of every segment,
+// so its columns are tc, tc + CW, ...) and release the stage through its
+// "empty" mbarrier.  Every F-hat pack serves all KB right-hand sides, so K of
+// them cost ceil(K / KB) passes over F-hat.  Bytes stay in flight while the
+// consumers do their (double-float) arithmetic.
 // ---------------------------------------------------------------------------
-template <class Kd, int R, int NCW, int STAGES>
+template <class Kd, int R, int KB, int NCW, int STAGES>
 __global__ void __launch_bounds__(32 * (NCW + 1), 2) gemv_n_kernel(GemvDesc d) {
   using Pack = typename Kd::Pack;
   using Acc = typename Kd::Acc;
   constexpr int NC = 32 * NCW;   // consumer threads
   constexpr int CW = NC;         // packs per row segment
-  constexpr int STAGE = (R + 1) * CW;
+  constexpr int STAGE = (R + KB) * CW;
+  static_assert(R * KB <= NC, "one consumer thread per output");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Pack* stage = reinterpret_cast<Pack*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(stage + STAGES * STAGE);
   uint64_t* empty = full + STAGES;
-  Acc* red = reinterpret_cast<Acc*>(empty + STAGES);   // [NCW][R]
+  Acc* red = reinterpret_cast<Acc*>(empty + STAGES);   // [NCW][R][KB]
 
-  const int w = blockIdx.y, b = blockIdx.z;
+  const int w = blockIdx.y, b0 = blockIdx.z * KB;
+  const int nbk = min(KB, d.K - b0);
   const int r0 = blockIdx.x * R;
   const int nr = min(R, d.Nd - r0);
   const int ldp = d.ldn / Kd::P;                        // packs per row
   const int nseg = (ldp + CW - 1) / CW;
   const Pack* F = static_cast<const Pack*>(d.F) + ((int64_t)w * d.Nd + r0) * ldp;
-  const Pack* x = static_cast<const Pack*>(d.x) + (b * d.x_ld_b + (int64_t)w * d.ldn) / Kd::P;
+  const Pack* x = static_cast<const Pack*>(d.x) + (b0 * d.x_ld_b + (int64_t)w * d.ldn) / Kd::P;
+  const int64_t xb = d.x_ld_b / Kd::P;                   // packs between right-hand sides
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -230,10 +235,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 2) gemv_n_kernel(GemvDesc d) {
         }
         const int p0 = c * CW;
         const uint32_t bytes = (uint32_t)min(CW, ldp - p0) * (uint32_t)sizeof(Pack);
-        mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)(nr + 1));
+        mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)(nr + nbk));
         Pack* st = stage + s * STAGE;
         for (int r = 0; r < nr; ++r) bulk_g2s_hint(st + r * CW, F + (int64_t)r * ldp + p0, bytes, &full[s], policy);
-        bulk_g2s(st + R * CW, x + p0, bytes, &full[s]);
+        for (int k = 0; k < nbk; ++k) bulk_g2s(st + (R + k) * CW, x + k * xb + p0, bytes, &full[s]);
       }
       // no copy may outlive the CTA: wait for the last issued stages to land
       for (int cc = max(0, c - STAGES); cc < c; ++cc)
@@ -245,9 +250,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 2) gemv_n_kernel(GemvDesc d) {
 
   // consumers
   const int tc = threadIdx.x - 32;
-  Acc acc[R];
+  Acc acc[R][KB];
 #pragma unroll
-  for (int r = 0; r < R; ++r) acc[r] = Kd::zero();
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int k = 0; k < KB; ++k) acc[r][k] = Kd::zero();
   for (int c = 0; c < nseg; ++c) {
     const int s = c % STAGES;
     if (!mbar_wait(&full[s], (c / STAGES) & 1)) {
@@ -256,32 +263,42 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 2) gemv_n_kernel(GemvDesc d) {
     }
     const Pack* st = stage + s * STAGE;
     if (tc < ldp - c * CW) {
-      // rows r >= nr (last row block only) hold stale shared memory; their
-      // accumulators are never stored
-      const Pack xv = st[R * CW + tc];
+      // rows r >= nr and right-hand sides k >= nbk (last blocks only) hold
+      // stale shared memory; their accumulators are never stored
+      Pack xv[KB];
 #pragma unroll
-      for (int r = 0; r < R; ++r) Kd::mac_n(acc[r], st[r * CW + tc], xv);
+      for (int k = 0; k < KB; ++k) xv[k] = st[(R + k) * CW + tc];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const Pack f = st[r * CW + tc];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) Kd::mac_n(acc[r][k], f, xv[k]);
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
   // reduction over the consumer threads: warp shuffles, then across warps
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
+  for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) acc[r] = Kd::add(acc[r], Kd::shfl_xor(acc[r], m));
-  }
+    for (int k = 0; k < KB; ++k)
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) acc[r][k] = Kd::add(acc[r][k], Kd::shfl_xor(acc[r][k], m));
   const int cw = warp - 1;
   if (lane == 0) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) red[cw * R + r] = acc[r];
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int k = 0; k < KB; ++k) red[(cw * R + r) * KB + k] = acc[r][k];
   }
   named_bar_sync(1, NC);
-  if (tc < nr) {
-    Acc sum = red[tc];
+  const int r = tc / KB, k = tc % KB;
+  if (tc < R * KB && r < nr && k < nbk) {
+    Acc sum = red[r * KB + k];
 #pragma unroll
-    for (int q = 1; q < NCW; ++q) sum = Kd::add(sum, red[q * R + tc]);
-    Kd::store(d.y, b * d.y_ld_b + (int64_t)w * d.Nd + r0 + tc, sum);
+    for (int q = 1; q < NCW; ++q) sum = Kd::add(sum, red[(q * R + r) * KB + k]);
+    Kd::store(d.y, (b0 + k) * d.y_ld_b + (int64_t)w * d.Nd + r0 + r, sum);
   }
 }
 
@@ -386,16 +403,21 @@ __global__ void convert_f32_kernel(const double2* __restrict__ in, float2* __res
 constexpr int kNR = 8, kNW = 8, kNS = 3;     // N: rows per CTA, consumer warps, pipeline stages
 constexpr int kHV = 2, kHT = 256, kHU = 4;   // H: packs per thread, threads, rows in flight
 
-template <class Kd>
-cudaError_t run_n(const GemvDesc& d, cudaStream_t s) {
-  auto kernel = gemv_n_kernel<Kd, kNR, kNW, kNS>;
-  const size_t smem = (size_t)kNS * (kNR + 1) * (32 * kNW) * sizeof(typename Kd::Pack) + 2 * kNS * sizeof(uint64_t) +
-                      (size_t)kNW * kNR * sizeof(typename Kd::Acc);
+template <class Kd, int R, int KB, int NCW, int STAGES>
+cudaError_t run_n_cfg(const GemvDesc& d, cudaStream_t s) {
+  auto kernel = gemv_n_kernel<Kd, R, KB, NCW, STAGES>;
+  const size_t smem = (size_t)STAGES * (R + KB) * (32 * NCW) * sizeof(typename Kd::Pack) +
+                      2 * STAGES * sizeof(uint64_t) + (size_t)NCW * R * KB * sizeof(typename Kd::Acc);
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((d.Nd + kNR - 1) / kNR, d.Nf, d.K);
-  kernel<<<grid, 32 * (kNW + 1), smem, s>>>(d);
+  dim3 grid((d.Nd + R - 1) / R, d.Nf, (d.K + KB - 1) / KB);
+  kernel<<<grid, 32 * (NCW + 1), smem, s>>>(d);
   return cudaGetLastError();
+}
+
+template <class Kd>
+cudaError_t run_n(const GemvDesc& d, cudaStream_t s) {
+  return run_n_cfg<Kd, kNR, 1, kNW, kNS>(d, s);
 }
 
 template <class Kd, int KB>
@@ -444,9 +466,11 @@ size_t fmt_bytes(int fmt) { return fmt == FMT_C64 ? 8 : 16; }
 cudaError_t launch_gemv_n(int kind, const GemvDesc& d, cudaStream_t s) {
   if (d.Nf == 0 || d.Nd == 0 || d.K == 0) return cudaSuccess;
   switch (kind) {
+    // one right-hand side: 8 rows per CTA; several: every F-hat pack feeds
+    // KB of them (FP64 stays at one: its FMA rate, not HBM, bounds it)
     case GEMV_F64: return run_n<KindF64>(d, s);
-    case GEMV_DF: return run_n<KindDF>(d, s);
-    default: return run_n<KindF32>(d, s);
+    case GEMV_DF: return d.K == 1 ? run_n<KindDF>(d, s) : run_n_cfg<KindDF, 2, 4, 4, 3>(d, s);
+    default: return d.K == 1 ? run_n<KindF32>(d, s) : run_n_cfg<KindF32, 4, 8, 4, 3>(d, s);
   }
 }
 
