@@ -272,6 +272,48 @@ template <typename P, bool INV> struct Dft<P, 8, INV> {
   }
 };
 
+// The same DFTs when the upper half of the inputs (q >= R/2) is zero: the
+// first forward pass, whose inputs t >= L/2 >= Nt are padding.
+template <typename P, int R, bool INV> struct DftHalf {
+  __device__ __forceinline__ static void run(typename Ar<P>::C* v) { Dft<P, R, INV>::run(v); }
+};
+template <typename P, bool INV> struct DftHalf<P, 2, INV> {
+  __device__ __forceinline__ static void run(typename Ar<P>::C* v) { v[1] = v[0]; }
+};
+template <typename P, bool INV> struct DftHalf<P, 4, INV> {
+  __device__ __forceinline__ static void run(typename Ar<P>::C* v) {
+    const typename Ar<P>::C a = v[0], c = v[1], d = Cx<P>::template mmi<INV>(v[1]);
+    v[0] = Cx<P>::add(a, c);
+    v[2] = Cx<P>::sub(a, c);
+    v[1] = Cx<P>::add(a, d);
+    v[3] = Cx<P>::sub(a, d);
+  }
+};
+template <typename P, bool INV> struct DftHalf<P, 8, INV> {
+  using A = Ar<P>;
+  using C = typename A::C;
+  __device__ __forceinline__ static void run(C* v) {
+    C e[4] = {v[0], v[2], v[4], v[6]};   // v[4], v[6] are zero
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    DftHalf<P, 4, INV>::run(e);
+    DftHalf<P, 4, INV>::run(o);
+    {
+      const C t = Cx<P>::template mmi<INV>(o[1]);
+      o[1] = Cx<P>::mulk(Cx<P>::add(o[1], t), KR2);
+    }
+    o[2] = Cx<P>::template mmi<INV>(o[2]);
+    {
+      const C t = Cx<P>::template mmi<INV>(o[3]);
+      o[3] = Cx<P>::mulk(Cx<P>::sub(t, o[3]), KR2);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      v[p] = Cx<P>::add(e[p], o[p]);
+      v[p + 4] = Cx<P>::sub(e[p], o[p]);
+    }
+  }
+};
+
 // Shared-memory layout: the NP complex signals of a CTA are interleaved,
 // element t of signal p at t * NP + p, so one time step (or frequency) of all
 // the CTA's channels is contiguous, like a row of the HBM arrays.  16-byte
@@ -289,7 +331,9 @@ __device__ __forceinline__ int sidx(int t, int p) { return swz<C>(t * NP + p); }
 // Butterfly j (< L/R) of signal p takes elements j + q L/R (q < R), applies the
 // twiddles exp(-+2 pi i q k / (Ns R)) of its position k = j mod Ns inside the
 // current sub-transform, and hands its R outputs to `dst` at (j - k) R + k + q Ns.
-// KMODE: 0 the first pass (Ns = 1, no twiddles), 1 a middle pass (k from a
+// KMODE: 0 the first forward pass (Ns = 1, no twiddles; for even R the inputs
+// q >= R/2 lie at t >= L/2 >= Nt, in the padding, and are neither read nor
+// added), 1 a middle pass (k from a
 // multiply-high by the plan's magic constant), 2 the last pass (Ns = L/R, so
 // k = j).  A thread keeps all its butterflies (at most E / R, rounded up) in
 // registers, so with SYNC_MID the pass runs in place on one shared buffer:
@@ -310,7 +354,10 @@ __device__ __forceinline__ void radix_pass(int T, int L, int Ns, int tws, unsign
     if (jt < nbt) {
       const int j = jt / NP, p = jt % NP;
 #pragma unroll
-      for (int q = 0; q < R; ++q) v[i][q] = src(j + q * nb, p, jt + q * nbt);
+      for (int q = 0; q < R; ++q) {
+        if (KMODE == 0 && R % 2 == 0 && q >= R / 2) v[i][q] = A::mk(A::zero(), A::zero());
+        else v[i][q] = src(j + q * nb, p, jt + q * nbt);
+      }
     }
   }
   if constexpr (SYNC_MID) __syncthreads();
@@ -331,7 +378,8 @@ __device__ __forceinline__ void radix_pass(int T, int L, int Ns, int tws, unsign
           v[i][q] = A::cmul(v[i][q], w);
         }
       }
-      Dft<P, R, INV>::run(v[i]);
+      if constexpr (KMODE == 0 && R % 2 == 0) DftHalf<P, R, INV>::run(v[i]);
+      else Dft<P, R, INV>::run(v[i]);
       const int base = (j - k) * R + k;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
@@ -581,13 +629,41 @@ __global__ void __launch_bounds__(1024, 1) rfft_fwd_kernel(FwdDesc d) {
       const int w = i / NG, g = i % NG;
       const int cg = g * G, c = c0 + cg;
       if (c >= d.out_cols) continue;
+      // the G/2 signals of this thread at w and L - w: 16-byte chunks (the
+      // swizzle moves whole chunks), so a warp reads rows conflict-free
+      C zw[G / 2], zc[G / 2];
+      const int wc = w == 0 ? 0 : L - w;
+      if constexpr (sizeof(C) == 8 && G >= 4) {
+#pragma unroll
+        for (int u = 0; u < G / 2; u += 2) {
+          const float4 a = *reinterpret_cast<const float4*>(buf + swz<C>(w * NP + cg / 2 + u));
+          const float4 bq = *reinterpret_cast<const float4*>(buf + swz<C>(wc * NP + cg / 2 + u));
+          zw[u] = A::mk(a.x, a.y);
+          zw[u + 1] = A::mk(a.z, a.w);
+          zc[u] = A::mk(bq.x, bq.y);
+          zc[u + 1] = A::mk(bq.z, bq.w);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < G / 2; ++u) {
+          zw[u] = buf[swz<C>(w * NP + cg / 2 + u)];
+          zc[u] = buf[swz<C>(wc * NP + cg / 2 + u)];
+        }
+      }
       __align__(16) __nv_bfloat16 h[4][G];   // rows: Re hi, Re lo, Im hi, Im lo
 #pragma unroll
       for (int u = 0; u < G; ++u) {
         float fr = 0.f, fi = 0.f;
         if (c + u < d.cols) {
+          const C z = zw[u >> 1], y = zc[u >> 1];
           R xr, xi;
-          split(w, cg + u, xr, xi);
+          if (u & 1) {
+            xr = A::half(A::add(A::im(z), A::im(y)));
+            xi = A::half(A::sub(A::re(y), A::re(z)));
+          } else {
+            xr = A::half(A::add(A::re(z), A::re(y)));
+            xi = A::half(A::sub(A::im(z), A::im(y)));
+          }
           fr = A::to_f(xr);
           fi = A::to_f(xi);
         }
