@@ -361,6 +361,46 @@ def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: in
             "algorithmic_bytes_per_call": int((Nt + 1) * Nd * Nm * 8 + K * Nt * Nm * 4 + K * Nt * Nd * 4)}
 
 
+def bench_hessian(torch, op, Fcol, stream, batch: int = 64, batches: int = 4) -> dict:
+    """Data-space Hessian columns H_d e_i = F(F* e_i) + noise (Remark 1), batch unit
+    vectors per F*/F pair on the tensor cores; the full matrix needs Nd*Nt columns."""
+    import numpy as np
+
+    from paper_2508_10202_gb300.hessian import hessian_columns
+    Nt, Nd, Nm = Fcol.shape
+    for w in ("F", "F*"):
+        op.set_precision(w, "sssss", "bf16x2")
+    rng = np.random.default_rng(11)
+    idx = rng.choice(Nt * Nd, size=batch * (batches + 1), replace=False)
+    with torch.cuda.stream(stream):
+        hessian_columns(op, idx[:batch], noise_var=1e-4, batch=batch, dtype=torch.float32, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        cols = hessian_columns(op, idx[batch:], noise_var=1e-4, batch=batch, dtype=torch.float32, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) * 1e-3
+    n = batch * batches
+    # spot check entries of the first timed column against the oracle's definition
+    i = int(idx[batch])
+    t, r = divmod(i, Nd)
+    probe = [((int(tt), int(rr)), (t, r)) for tt, rr in zip(rng.integers(Nt, size=6), rng.integers(Nd, size=6))]
+    probe.append(((t, r), (t, r)))
+    ref = oracle_hessian_entries(Fcol, probe, noise_var=1e-4)
+    got = np.array([float(cols[0, tt, rr]) for (tt, rr), _ in probe])
+    return {"columns": n, "batch": batch, "seconds": s, "columns_per_s": n / s,
+            "full_assembly_s_projected": Nt * Nd / (n / s),
+            "prec": "sssss/bf16x2 both directions (tensor cores)",
+            "rel_err_sampled": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+
+
+def oracle_hessian_entries(Fcol, pairs, noise_var):
+    import oracle
+    return oracle.hessian_entries(Fcol, pairs, noise_var=noise_var)
+
+
 # the served mix: four resident operators (Nt, Nd, Nm), blocks N(0,1) in float32
 SERVE_OPS = {"op128": (128, 16, 1000), "op256": (256, 64, 4000), "op500": (500, 100, 10000),
              "op1000": (1000, 200, 8000)}
@@ -588,6 +628,10 @@ def main(args) -> None:
     if rank == 0 and not args.no_multi:
         multi = {w: bench_multi_rhs(torch, op, Fcol, dev, stream, (peak, peak_kind), which=w) for w in ("F", "F*")}
 
+    hess = None
+    if rank == 0 and not args.no_multi:
+        hess = bench_hessian(torch, op, Fcol, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(Fcol, m, d)
@@ -611,7 +655,7 @@ def main(args) -> None:
             "gpu_launches": KERNELS_PER_MATVEC * 2 * args.steps,
             "rel_err": {"F": err_f, "Fstar": err_a, "how": "24 sampled outputs vs the oracle's definition"},
             "roofline": roofline, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "variants": variants,
-            "multi_rhs": multi, "pareto": pareto, "served": served,
+            "multi_rhs": multi, "hessian": hess, "pareto": pareto, "served": served,
             "served_p50_ms": served["load_0.9"]["p50_ms"] if served else None,
             "served_p99_ms": served["load_0.9"]["p99_ms"] if served else None,
             "setup_s": t_setup, "gen_s": t_gen,

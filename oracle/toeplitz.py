@@ -42,6 +42,7 @@ __all__ = [
     "spectrum", "matvec_fft", "rmatvec_fft", "matvec_fft_spec", "rmatvec_fft_spec",
     "matvec_mixed", "rmatvec_mixed", "parse_precision",
     "matvec_entries", "rmatvec_entries", "relative_error_bound", "rel_l2",
+    "hessian_entries",
 ]
 
 
@@ -330,3 +331,25 @@ def relative_error_bound(prec: str, Nt: int, n_inner: int, kappa: float, p: int 
     if p > 1:
         bound += e[4] * np.log2(p)
     return float(kappa * bound + c5 * e[4])
+
+
+# ---------------------------------------------------------------------------
+# Data-space Hessian, Section 2 (Gaussian prior and noise) and Remark 1
+# ---------------------------------------------------------------------------
+
+def hessian_entries(Fcol: np.ndarray, pairs, prior_var: float = 1.0, noise_var: float = 0.0) -> np.ndarray:
+    """Entries of H_d = F G_prior F* + G_noise with isotropic covariances.
+
+    G_prior = prior_var I and G_noise = noise_var I.  For data indices
+    (t1, r1), (t2, r2) the block-Toeplitz structure gives
+        H_d[(t1, r1), (t2, r2)] = prior_var sum_{j <= min(t1, t2)} sum_n F_{t1-j}[r1, n] F_{t2-j}[r2, n]
+                                  + noise_var [t1 == t2 and r1 == r2],
+    the inner product of rows (t1, r1) and (t2, r2) of the dense matrix.
+    """
+    Fcol = np.asarray(Fcol, dtype=np.float64)
+    out = np.empty(len(pairs))
+    for k, ((t1, r1), (t2, r2)) in enumerate(pairs):
+        j = np.arange(min(t1, t2) + 1)
+        acc = float(np.sum(Fcol[t1 - j, r1, :] * Fcol[t2 - j, r2, :]))
+        out[k] = prior_var * acc + (noise_var if (t1, r1) == (t2, r2) else 0.0)
+    return out

@@ -330,3 +330,31 @@ def test_perturb_mantissa():
         assert a != b and abs(a - b) <= 2.0 ** -23 * abs(a)
         assert np.float64(np.float32(b)) != b          # not FP32-exact any more
         assert (np.float64(b).view(np.uint64) & np.uint64((1 << 29) - 1)) == (1 << 29) - 1
+
+
+# --- data-space Hessian entries (Section 2, Remark 1) ------------------------
+
+def test_hessian_entries_match_dense_gram():
+    # H_d = prior F F^T + noise I: rows of the dense matrix, entry by entry
+    Nt, Nd, Nm = 7, 3, 5
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=8)
+    A = oracle.dense_matrix(Fcol)
+    H = 0.7 * A @ A.T + 0.05 * np.eye(Nt * Nd)
+    rng = np.random.default_rng(0)
+    pairs = [((int(a), int(b)), (int(c), int(e))) for a, b, c, e in
+             zip(rng.integers(Nt, size=40), rng.integers(Nd, size=40), rng.integers(Nt, size=40), rng.integers(Nd, size=40))]
+    pairs += [((3, 1), (3, 1)), ((0, 0), (6, 2))]
+    got = oracle.hessian_entries(Fcol, pairs, prior_var=0.7, noise_var=0.05)
+    ref = np.array([H[t1 * Nd + r1, t2 * Nd + r2] for (t1, r1), (t2, r2) in pairs])
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(H).max())
+
+
+def test_hessian_entries_identity_operator():
+    # F_0 = I, F_k = 0: F F^T = I, so H_d = (prior + noise) I exactly
+    Nt, N = 5, 4
+    Fcol = np.zeros((Nt, N, N))
+    Fcol[0] = np.eye(N)
+    pairs = [((t, r), (t2, r2)) for t in range(Nt) for r in range(N) for t2 in (0, t) for r2 in (0, r)]
+    got = oracle.hessian_entries(Fcol, pairs, prior_var=2.0, noise_var=0.25)
+    ref = np.array([2.25 if (a == b) else 0.0 for a, b in pairs])
+    np.testing.assert_array_equal(got, ref)
