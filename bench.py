@@ -55,8 +55,9 @@ VARIANTS = {
     "all_fp32": (("sssss", "native", "native"), ("sssss", "native", "native")),
 }
 KERNELS_PER_MATVEC = 3
-# mean DRAM bytes per launch of gemv_n/gemv_h<KindDF> at the paper shape
-GEMV_DF_TRAFFIC = 16.15e9
+# mean DRAM bytes per launch of gemv_n/gemv_h<KindDF> at the paper shape (ncu dram__bytes
+# read + write on Nm=2000, 3.238e9 and 3.212e9 B, scaled by 5 in Nm)
+GEMV_DF_TRAFFIC = 16.12e9
 
 
 def parse_args(argv=None):

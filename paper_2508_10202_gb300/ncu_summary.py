@@ -20,7 +20,8 @@ def main(path, n_setup=0):
     launches = []
     for r in rows[start + 1:]:
         if len(r) > vi and r[mi] == "gpu__time_duration.sum":
-            name = re.sub(r"\(.*", "", r[ki]).replace("(anonymous namespace)::", "").replace("unnamed>::", "")
+            name = re.sub(r"\(.*", "", r[ki].replace("(anonymous namespace)::", ""))
+            name = name.replace("fftmv::<unnamed>::", "").replace("unnamed>::", "").replace("fftmv::", "")
             launches.append((name, float(r[vi].replace(",", "")) * scale[r[ui]]))
     for title, part in (("setup", launches[:n_setup]), ("matvec", launches[n_setup:])):
         agg = collections.OrderedDict()
