@@ -1,25 +1,28 @@
 // Multi-right-hand-side block matvec on the 5th-generation tensor cores
-// (tcgen05), for the forward operator F: for every frequency w,
-//     D-hat_w (Nd x K) = F-hat_w (Nd x Nm) * M-hat_w (Nm x K)      (complex)
+// (tcgen05), both directions: for every frequency w
+//     F:  D-hat_w (Nd x K) = F-hat_w (Nd x Nm) * M-hat_w (Nm x K)
+//     F*: M-hat_w (Nm x K) = F-hat_w^H (Nm x Nd) * D-hat_w (Nd x K)   (complex)
 // the per-frequency product of Section 2.4 phase 3 applied to K right-hand
 // sides at once, which turns the batched GEMV into a dense contraction.
 //
-// Precision: F-hat and M-hat are each split into bfloat16 hi + lo parts
+// Precision: F-hat and the spectra are each split into bfloat16 hi + lo parts
 // (x = hi + lo + O(2^-18 |x|)); the three products hi*hi + hi*lo + lo*hi
 // accumulate in FP32 in tensor memory (the lo*lo term is below 2^-16 of the
 // result).
 //
 // Complex arithmetic without duplicating data: A is four planes
-// (Re hi, Re lo, Im hi, Im lo) of F-hat_w, B is [Re M | Im M] (2*KC columns,
+// (Re hi, Re lo, Im hi, Im lo) of F-hat_w, B is [Re X | Im X] (2*KC columns,
 // hi and lo planes).  Two accumulators: acc1 = Re(F) * B, acc2 = Im(F) * B;
-// then Re D = acc1[:, q] - acc2[:, KC + q] and Im D = acc1[:, KC + q] + acc2[:, q].
+// then Re D = acc1[:, q] - acc2[:, KC + q] and Im D = acc1[:, KC + q] + acc2[:, q]
+// (the acc2 signs flip for conj(F)).  F* reads the same A planes transposed
+// through an MN-major descriptor.
 //
-// Per CTA: one frequency w, one chunk of KC <= 64 right-hand sides and one
-// tile of 128 rows; MMA tile M = 128 (rows >= Nd are zero-filled by TMA, never
-// read from HBM),
-// N = 2*KC rounded up to 16, K-step 64 bf16 (one 128-byte swizzled row).
+// Tiles: one frequency, one chunk of KC <= 64 right-hand sides and 128 output
+// rows; MMA tile M = 128 (rows past the end are zero-filled by TMA, never read
+// from HBM), N = 2*KC rounded up to 16, K-step 64 bf16 (one 128-byte swizzled
+// row).  Persistent CTAs, one per SM, loop over the tiles.
 // Warp roles: warp 0 issues TMA loads, warp 1 owns tensor memory and issues
-// the MMAs, warps 2-9 drain the accumulators (tcgen05.ld) and write D-hat.
+// the MMAs, warps 2-9 drain the accumulators (tcgen05.ld) and write the output.
 //
 // Accumulation in groups: the tensor core's internal FP32 accumulation loses
 // accuracy over long contractions (10^4 terms here), so the MMAs accumulate
