@@ -314,6 +314,121 @@ template <typename P, bool INV> struct DftHalf<P, 8, INV> {
   }
 };
 
+// --- composite radices in registers -----------------------------------------
+// cos and sin of 2 pi m / n at compile time: quadrant reduction (exact: the
+// quadrant's cosine and sine are 0 and +-1), then Taylor series on
+// |x| <= pi/4, whose 14 terms leave an error below 1e-30.
+__host__ __device__ constexpr double taylor_sin(double x) {
+  double t = x, s = x;
+  for (int k = 1; k < 14; ++k) {
+    t *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    s += t;
+  }
+  return s;
+}
+__host__ __device__ constexpr double taylor_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int k = 1; k < 14; ++k) {
+    t *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    s += t;
+  }
+  return s;
+}
+// (cos, sin) of 2 pi m / n: quadrant q = round(4 m / n), x = 2 pi (m/n - q/4)
+__host__ __device__ constexpr double cos_2pi(int m, int n) {
+  const int r = ((m % n) + n) % n;
+  const int q = (8 * r + n) / (2 * n);                  // nearest quadrant, 0..4
+  const double x = 2.0 * 3.14159265358979323846264338327950288 * ((double)(4 * r - q * n) / (4.0 * n));
+  switch (q & 3) {
+    case 0: return taylor_cos(x);
+    case 1: return -taylor_sin(x);
+    case 2: return -taylor_cos(x);
+    default: return taylor_sin(x);
+  }
+}
+__host__ __device__ constexpr double sin_2pi(int m, int n) {
+  const int r = ((m % n) + n) % n;
+  const int q = (8 * r + n) / (2 * n);
+  const double x = 2.0 * 3.14159265358979323846264338327950288 * ((double)(4 * r - q * n) / (4.0 * n));
+  switch (q & 3) {
+    case 0: return taylor_sin(x);
+    case 1: return taylor_cos(x);
+    case 2: return -taylor_sin(x);
+    default: return -taylor_cos(x);
+  }
+}
+__host__ __device__ constexpr Kc kc_of(double v) { return Kc{v, (float)v, (float)(v - (double)(float)v)}; }
+
+// W_R^m = exp(-2 pi i m / R) for m < R, in every precision
+template <int R> struct TwTab {
+  Kc c[R], s[R];
+};
+template <int R>
+__host__ __device__ constexpr TwTab<R> make_twtab() {
+  TwTab<R> t{};
+  for (int m = 0; m < R; ++m) {
+    t.c[m] = kc_of(cos_2pi(m, R));
+    t.s[m] = kc_of(sin_2pi(m, R));
+  }
+  return t;
+}
+__device__ constexpr TwTab<16> kTw16 = make_twtab<16>();
+__device__ constexpr TwTab<25> kTw25 = make_twtab<25>();
+template <int R> __device__ __forceinline__ const TwTab<R>& twtab();
+template <> __device__ __forceinline__ const TwTab<16>& twtab<16>() { return kTw16; }
+template <> __device__ __forceinline__ const TwTab<25>& twtab<25>() { return kTw25; }
+
+// DFT of size R = R1 R2 in registers (Cooley-Tukey with constant twiddles):
+//   X[k1 + R1 k2] = sum_n2 W_R2^(n2 k2) W_R^(n2 k1) sum_n1 W_R1^(n1 k1) x[n1 R2 + n2]
+// HALF: inputs n >= R/2 are zero, i.e. n1 >= R1/2 in every inner DFT.
+template <typename P, int R1, int R2, bool INV, bool HALF> struct DftComp {
+  using A = Ar<P>;
+  using C = typename A::C;
+  static constexpr int R = R1 * R2;
+  __device__ __forceinline__ static void run(C* v) {
+    const TwTab<R>& tt = twtab<R>();
+    C y[R];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+      C u[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) u[n1] = v[n1 * R2 + n2];
+      if constexpr (HALF) DftHalf<P, R1, INV>::run(u);
+      else Dft<P, R1, INV>::run(u);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) {
+        const int m = (n2 * k1) % R;
+        if (m == 0) {
+          y[n2 * R1 + k1] = u[k1];
+        } else {   // u * (c -+ i s)
+          const typename A::R re = A::re(u[k1]), im = A::im(u[k1]);
+          const typename A::R cr = A::mulk(re, tt.c[m]), ci = A::mulk(im, tt.c[m]);
+          const typename A::R sr = A::mulk(re, tt.s[m]), si = A::mulk(im, tt.s[m]);
+          y[n2 * R1 + k1] = INV ? A::mk(A::sub(cr, si), A::add(ci, sr)) : A::mk(A::add(cr, si), A::sub(ci, sr));
+        }
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C w[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) w[n2] = y[n2 * R1 + k1];
+      Dft<P, R2, INV>::run(w);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = w[k2];
+    }
+  }
+};
+template <typename P, bool INV> struct Dft<P, 16, INV> {
+  __device__ __forceinline__ static void run(typename Ar<P>::C* v) { DftComp<P, 4, 4, INV, false>::run(v); }
+};
+template <typename P, bool INV> struct Dft<P, 25, INV> {
+  __device__ __forceinline__ static void run(typename Ar<P>::C* v) { DftComp<P, 5, 5, INV, false>::run(v); }
+};
+template <typename P, bool INV> struct DftHalf<P, 16, INV> {
+  __device__ __forceinline__ static void run(typename Ar<P>::C* v) { DftComp<P, 4, 4, INV, true>::run(v); }
+};
+
 // Shared-memory layout: the NP complex signals of a CTA are interleaved,
 // element t of signal p at t * NP + p, so one time step (or frequency) of all
 // the CTA's channels is contiguous, like a row of the HBM arrays.  16-byte
@@ -448,8 +563,8 @@ __host__ __device__ constexpr int fft_pairs(int L) {
   return np;
 }
 template <typename P>
-__host__ __device__ constexpr int fft_nthreads(int np, int L) {
-  const int t = ((np * L + kFftE<P> - 1) / kFftE<P> + 31) / 32 * 32;
+__host__ __device__ constexpr int fft_nthreads(int np, int L, int e = kFftE<P>) {
+  const int t = ((np * L + e - 1) / e + 31) / 32 * 32;
   return t < 64 ? 64 : t;
 }
 
@@ -462,16 +577,28 @@ struct CPlan {
   int rad[kMaxPasses];
   int ns[kMaxPasses];
 };
-// the same radix order as make_plan: 8, 4, 2, 5, 3
+// FP64 and double-float: the same radix order as make_plan (8, 4, 2, 5, 3).
+// FP32 keeps up to 25 complexes per thread in registers, so its plans use the
+// composite radices 16 and 25 and need fewer passes through shared memory:
+// 2000 = 16 5 25, 1000 = 8 5 25, 256 = 16 16, 128 = 16 8.
+template <typename P>
 __host__ __device__ constexpr CPlan cplan(int L) {
   CPlan p{};
-  int n = L, np = 0;
-  const int order[5] = {8, 4, 2, 5, 3};
-  for (int o = 0; o < 5; ++o)
-    while (n % order[o] == 0) {
-      p.rad[np++] = order[o];
-      n /= order[o];
-    }
+  int np = 0;
+  if (std::is_same<P, float>::value && (L == 2000 || L == 1000 || L == 256 || L == 128)) {
+    const int r2000[3] = {16, 5, 25}, r1000[3] = {8, 5, 25}, r256[2] = {16, 16}, r128[2] = {16, 8};
+    const int* r = L == 2000 ? r2000 : L == 1000 ? r1000 : L == 256 ? r256 : r128;
+    np = (L >= 1000) ? 3 : 2;
+    for (int i = 0; i < np; ++i) p.rad[i] = r[i];
+  } else {
+    int n = L;
+    const int order[5] = {8, 4, 2, 5, 3};
+    for (int o = 0; o < 5; ++o)
+      while (n % order[o] == 0) {
+        p.rad[np++] = order[o];
+        n /= order[o];
+      }
+  }
   p.npass = np;
   int ns = 1;
   for (int i = 0; i < np; ++i) {
@@ -480,6 +607,21 @@ __host__ __device__ constexpr CPlan cplan(int L) {
   }
   return p;
 }
+// complex elements a thread holds during a pass of the length-L kernel
+template <typename P>
+__host__ __device__ constexpr int fft_elems(int L) {
+  return (std::is_same<P, float>::value && (L == 2000 || L == 1000)) ? 25 : kFftE<P>;
+}
+// launch bounds of the length-L kernel: 25-element threads get up to 102
+// registers (320 threads, two CTAs per SM); the others 64
+template <typename P>
+__host__ __device__ constexpr int fft_bound_threads(int LC) {
+  return LC > 0 && fft_elems<P>(LC) == 25 ? 320 : 1024;
+}
+template <typename P>
+__host__ __device__ constexpr int fft_bound_blocks(int LC) {
+  return LC > 0 && fft_elems<P>(LC) == 25 ? 2 : 1;
+}
 __host__ __device__ constexpr unsigned cmagic(int ns) {
   return ns > 1 ? (unsigned)((((unsigned long long)1 << 32) + (unsigned long long)ns - 1) / (unsigned long long)ns) : 0u;
 }
@@ -487,7 +629,7 @@ __host__ __device__ constexpr unsigned cmagic(int ns) {
 // pass PS of the length-L plan
 template <typename P, bool INV, int NP, int E, int L, int PS, int KMODE, bool SYNC_MID, class Src, class Dst>
 __device__ __forceinline__ void cpass(int T, const typename Ar<P>::C* __restrict__ tw, Src src, Dst dst) {
-  constexpr CPlan pl = cplan(L);
+  constexpr CPlan pl = cplan<P>(L);
   constexpr int R = pl.rad[PS], Ns = pl.ns[PS];
   radix_pass<P, R, INV, NP, E, KMODE, SYNC_MID>(T, L, Ns, L / (Ns * R), cmagic(Ns), tw, src, dst);
 }
@@ -562,15 +704,15 @@ __device__ __forceinline__ typename Ar<P>::C load_cx(const void* X, int64_t i, i
 // other passes run in place in shared memory, then the real/imaginary split
 // writes the spectra.
 template <typename Tin, typename P, int NP, int LC>
-__global__ void __launch_bounds__(1024, 1) rfft_fwd_kernel(FwdDesc d) {
+__global__ void __launch_bounds__(fft_bound_threads<P>(LC), fft_bound_blocks<P>(LC)) rfft_fwd_kernel(FwdDesc d) {
   using A = Ar<P>;
   using C = typename A::C;
   using R = typename A::R;
-  constexpr int E = kFftE<P>;
+  constexpr int E = LC > 0 ? fft_elems<P>(LC) : kFftE<P>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int L = LC > 0 ? LC : d.plan.L;
-  const int T = LC > 0 ? fft_nthreads<P>(NP, LC) : (int)blockDim.x;
+  const int T = LC > 0 ? fft_nthreads<P>(NP, LC, fft_elems<P>(LC)) : (int)blockDim.x;
   const int Nf = L / 2 + 1;
   constexpr int NCH = 2 * NP;
   const int groups = (d.out_cols + NCH - 1) / NCH;
@@ -594,7 +736,7 @@ __global__ void __launch_bounds__(1024, 1) rfft_fwd_kernel(FwdDesc d) {
   if constexpr (LC > 0) {
     cpass<P, false, NP, E, LC, 0, 0, false>(T, tw, gsrc, sdst);
     __syncthreads();
-    cpasses<P, false, NP, E, LC, 1, cplan(LC).npass>(T, tw, ssrc, sdst);
+    cpasses<P, false, NP, E, LC, 1, cplan<P>(LC).npass>(T, tw, ssrc, sdst);
   } else {
     any_pass<P, false, NP, E, 0, false>(d.plan, 0, tw, gsrc, sdst);
     __syncthreads();
@@ -706,14 +848,14 @@ __device__ __forceinline__ void store_real(void* y, int64_t i, typename Ar<P>::R
 // place, and the last pass writes t < Nt straight to HBM (1/L scale, unpad and
 // output cast fused).
 template <typename P, typename Tout, int NP, int LC>
-__global__ void __launch_bounds__(1024, 1) irfft_inv_kernel(InvDesc d) {
+__global__ void __launch_bounds__(fft_bound_threads<P>(LC), fft_bound_blocks<P>(LC)) irfft_inv_kernel(InvDesc d) {
   using A = Ar<P>;
   using C = typename A::C;
-  constexpr int E = kFftE<P>;
+  constexpr int E = LC > 0 ? fft_elems<P>(LC) : kFftE<P>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int L = LC > 0 ? LC : d.plan.L;
-  const int T = LC > 0 ? fft_nthreads<P>(NP, LC) : (int)blockDim.x;
+  const int T = LC > 0 ? fft_nthreads<P>(NP, LC, fft_elems<P>(LC)) : (int)blockDim.x;
   const int Nf = L / 2 + 1;
   constexpr int NCH = 2 * NP;
   const int c0 = blockIdx.x * NCH;
@@ -752,7 +894,7 @@ __global__ void __launch_bounds__(1024, 1) irfft_inv_kernel(InvDesc d) {
   const C* tw = static_cast<const C*>(d.tw);
   auto sdst = [&](int, int, int e, C v) { buf[swz<C>(e)] = v; };
   auto ssrc = [&](int, int, int e) -> C { return buf[swz<C>(e)]; };
-  if constexpr (LC > 0) cpasses<P, true, NP, E, LC, 0, cplan(LC).npass - 1>(T, tw, ssrc, sdst);
+  if constexpr (LC > 0) cpasses<P, true, NP, E, LC, 0, cplan<P>(LC).npass - 1>(T, tw, ssrc, sdst);
   else inplace_passes<P, true, NP, E>(d.plan, 0, d.plan.npass - 1, tw, ssrc, sdst);
   const Kc inv_L{d.inv_L, d.inv_L_hi, d.inv_L_lo};
   auto gdst = [&](int t, int p, int, C v) {
@@ -762,7 +904,7 @@ __global__ void __launch_bounds__(1024, 1) irfft_inv_kernel(InvDesc d) {
     store_real<Tout, P>(d.y, o, A::mulk(A::re(v), inv_L), d.unpad_single);
     if (c + 1 < d.cols) store_real<Tout, P>(d.y, o + 1, A::mulk(A::im(v), inv_L), d.unpad_single);
   };
-  if constexpr (LC > 0) cpass<P, true, NP, E, LC, cplan(LC).npass - 1, 2, false>(T, tw, ssrc, gdst);
+  if constexpr (LC > 0) cpass<P, true, NP, E, LC, cplan<P>(LC).npass - 1, 2, false>(T, tw, ssrc, gdst);
   else any_pass<P, true, NP, E, 2, false>(d.plan, d.plan.npass - 1, tw, ssrc, gdst);
 }
 
@@ -778,7 +920,7 @@ cudaError_t fwd_launch_np(const FwdDesc& d, cudaStream_t s) {
   const int groups = (d.out_cols + 2 * NP - 1) / (2 * NP);
   dim3 grid(d.rows * groups, d.K);
   const size_t smem = (size_t)NP * d.plan.L * sizeof(typename Ar<P>::C);
-  const int threads = fft_nthreads<P>(NP, d.plan.L);
+  const int threads = LC > 0 ? fft_nthreads<P>(NP, LC, fft_elems<P>(LC)) : fft_nthreads<P>(NP, d.plan.L);
   if (threads > 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = prep(rfft_fwd_kernel<Tin, P, NP, LC>, smem);
   if (e != cudaSuccess) return e;
@@ -790,7 +932,7 @@ template <typename P, typename Tout, int NP, int LC>
 cudaError_t inv_launch_np(const InvDesc& d, cudaStream_t s) {
   dim3 grid((d.cols + 2 * NP - 1) / (2 * NP), d.K);
   const size_t smem = (size_t)NP * d.plan.L * sizeof(typename Ar<P>::C);
-  const int threads = fft_nthreads<P>(NP, d.plan.L);
+  const int threads = LC > 0 ? fft_nthreads<P>(NP, LC, fft_elems<P>(LC)) : fft_nthreads<P>(NP, d.plan.L);
   if (threads > 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = prep(irfft_inv_kernel<P, Tout, NP, LC>, smem);
   if (e != cudaSuccess) return e;
