@@ -26,8 +26,12 @@
  * (including managed memory) or host pointers; the library asks the CUDA
  * runtime which.  Device I/O is stream ordered and asynchronous: the caller
  * keeps the buffers alive until the stream has run the work.  Host I/O is
- * staged through device memory and the call returns after the result has
- * reached host memory.
+ * staged through device memory.  When every host buffer of a call is
+ * page-locked (cudaHostAlloc / cudaHostRegister), the copies are stream
+ * ordered too and the call returns at once: the result is in host memory once
+ * the stream has run the work, so calls on several streams overlap one call's
+ * copies with another's kernels.  With pageable host memory the call returns
+ * after the result has reached host memory.
  *
  * Errors.  Every entry point returns an fftmv_status.  Nothing aborts, traps
  * or throws across the ABI.  On failure fftmv_last_error() returns a message

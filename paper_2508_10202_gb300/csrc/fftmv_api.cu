@@ -83,6 +83,17 @@ FftPlan make_plan(int64_t L) {
   return p;
 }
 
+// page-locked host memory (cudaHostAlloc / cudaHostRegister): copies to and
+// from it are truly asynchronous
+bool is_pinned_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -382,7 +393,9 @@ int run_matvec(fftmv_op* op, int which, const void* in, void* out, int64_t K, in
   cudaError_t ef = cudaFreeAsync(ws, s);
   if (e != cudaSuccess) return cuda_fail(e, "matvec kernels");
   if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
-  if (!in_dev || !out_dev) CUDA_TRY(cudaStreamSynchronize(s));
+  // pageable host buffers: return once the result is in host memory; page-locked
+  // ones stay stream ordered like device I/O
+  if ((!in_dev && !is_pinned_host(in)) || (!out_dev && !is_pinned_host(out))) CUDA_TRY(cudaStreamSynchronize(s));
   return FFTMV_OK;
 }
 

@@ -186,7 +186,11 @@ class Operator:
         return out
 
     def matvec(self, m, out=None, stream=None):
-        """d = F m (Section 2.4): m is (Nt, Nm) or (K, Nt, Nm); returns (.., Nt, Nd)."""
+        """d = F m (Section 2.4): m is (Nt, Nm) or (K, Nt, Nm); returns (.., Nt, Nd).
+
+        Device tensors, and host tensors that are all pinned, run stream ordered
+        (synchronise the stream before reading ``out``); with a pageable host
+        buffer the call returns with the result in place."""
         return self._apply(L.FFTMV_FORWARD, m, out, stream)
 
     def rmatvec(self, d, out=None, stream=None):

@@ -202,6 +202,32 @@ def test_fp32_io_and_host_io(torch_cuda):
     op.free()
 
 
+def test_pinned_host_io_is_stream_ordered(torch_cuda):
+    # every host buffer pinned: the calls return at once and the result lands in
+    # host memory when the stream has run them; several streams in flight
+    torch = torch_cuda
+    Fcol, m, d = make_case(40, 6, 33, K=2, seed=12)
+    op = gpu_op(torch, Fcol)
+    for w in ("F", "F*"):
+        op.set_precision(w, "ddddd", "f64x2f32")
+    y_ref = op.matvec(torch.from_numpy(m).cuda()).cpu().numpy()
+    x_ref = op.rmatvec(torch.from_numpy(d).cuda()).cpu().numpy()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for i in range(6):
+        mp, dp = torch.from_numpy(m).pin_memory(), torch.from_numpy(d).pin_memory()
+        yp = torch.empty(y_ref.shape, dtype=torch.float64).pin_memory()
+        xp = torch.empty(x_ref.shape, dtype=torch.float64).pin_memory()
+        op.matvec(mp, out=yp, stream=streams[i % 2])
+        op.rmatvec(dp, out=xp, stream=streams[i % 2])
+        outs.append((mp, dp, yp, xp))
+    torch.cuda.synchronize()
+    for _, _, yp, xp in outs:
+        np.testing.assert_array_equal(yp.numpy(), y_ref)
+        np.testing.assert_array_equal(xp.numpy(), x_ref)
+    op.free()
+
+
 def test_host_block_column_equals_device_block_column(torch_cuda):
     torch = torch_cuda
     from paper_2508_10202_gb300 import Operator
