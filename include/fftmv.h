@@ -132,7 +132,8 @@ int fftmv_get_precision(const fftmv_op* op, int which, fftmv_precision* out);
 /* d = F m for K right-hand sides (Section 2.4, phases 1-5).
  *   m : K*Nt*Nm values [b][j][n]; d : K*Nt*Nd values [b][i][r].
  *   io_dtype : FFTMV_IO_F64 or FFTMV_IO_F32 for both m and d.
- *   K >= 0 (K = 0 does nothing).  m and d must not overlap. */
+ *   K >= 0 (K = 0 does nothing).  m and d must not overlap.  Large K runs in
+ *   chunks within the scratch bound (fftmv_set_scratch_limit). */
 int fftmv_matvec(fftmv_op* op, const void* m, void* d, int64_t K, int io_dtype, void* stream);
 
 /* m = F* d for K right-hand sides: the same phases with the conjugate
@@ -143,6 +144,15 @@ int fftmv_rmatvec(fftmv_op* op, const void* d, void* m, int64_t K, int io_dtype,
 /* Device scratch one call takes from the operator's stream-ordered pool
  * (which = FORWARD or ADJOINT), not counting host-I/O staging. */
 int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out);
+
+/* Bound on the scratch one launch sequence of fftmv_matvec / fftmv_rmatvec
+ * takes from the pool (spectra plus host-I/O staging).  A call whose K
+ * right-hand sides need more runs them in chunks of the most that fit (whole
+ * 64-RHS chunks on the tensor cores), back to back on the stream; results do
+ * not depend on the chunking beyond rounding order.  bytes = 0 restores the
+ * default, 8 GiB.  A single right-hand side always runs, whatever the bound.
+ * Errors: EINVAL / ESTATE for a bad handle. */
+int fftmv_set_scratch_limit(fftmv_op* op, size_t bytes);
 
 /* F m (which = FFTMV_FORWARD) or F* d (FFTMV_ADJOINT) with caller-supplied
  * scratch, so a serving layer can own and account for every byte and capture

@@ -131,6 +131,7 @@ struct fftmv_op {
   std::vector<TimingSet> free_sets, pending;
   double acc_ms[2][3] = {};
   int64_t calls[2] = {};
+  size_t scratch_limit = 0;  // 0: kCallScratchBudget
 };
 
 namespace {
@@ -327,26 +328,39 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   return e;
 }
 
-int run_matvec(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io, void* stream) {
-  int rc = check_op(op);
-  if (rc) return rc;
-  if (K < 0) return fail(FFTMV_EINVAL, "K = %lld < 0", (long long)K);
-  if (io != FFTMV_IO_F64 && io != FFTMV_IO_F32) return fail(FFTMV_EINVAL, "io_dtype %d unknown", io);
-  if (K == 0) return FFTMV_OK;
-  if (!in || !out) return fail(FFTMV_EINVAL, "null input or output");
-  if (K > 65535) return fail(FFTMV_EUNSUPPORTED, "K = %lld exceeds 65535 right-hand sides per call", (long long)K);
-  DeviceGuard dg(op->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// Scratch of one call: the two spectra plus the staging of host I/O.
+size_t call_scratch(const fftmv_op* op, int which, int64_t K, size_t esz, bool stage_in, bool stage_out) {
+  const CallPlan c = plan_call(op, which, K);
+  size_t b = c.in_hat + c.out_hat;
+  if (stage_in) b += align256((size_t)K * op->Nt * c.Cin * esz);
+  if (stage_out) b += align256((size_t)K * op->Nt * c.Cout * esz);
+  return b;
+}
+
+// Right-hand sides per launch sequence: all K while the scratch stays within
+// kCallScratchBudget, else the most that fit (whole 64-RHS chunks on the
+// tensor cores); the chunks run back to back on the stream.
+constexpr size_t kCallScratchBudget = (size_t)8 << 30;
+int64_t rhs_per_chunk(const fftmv_op* op, int which, int64_t K, size_t esz, bool stage_in, bool stage_out) {
+  const size_t budget = op->scratch_limit ? op->scratch_limit : kCallScratchBudget;
+  if (call_scratch(op, which, K, esz, stage_in, stage_out) <= budget) return K;
+  int64_t lo = 1, hi = K;   // scratch grows with K
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (call_scratch(op, which, mid, esz, stage_in, stage_out) <= budget) lo = mid;
+    else hi = mid - 1;
+  }
+  if (gemv_kind(op->prec[which]) == GEMV_TC && lo >= 64) lo = lo / 64 * 64;
+  return lo;
+}
+
+// One launch sequence over K right-hand sides (no final host synchronisation).
+int run_chunk(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io, cudaStream_t s, bool in_dev,
+              bool out_dev) {
   const CallPlan c = plan_call(op, which, K);
   const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
   const size_t in_bytes = (size_t)K * op->Nt * c.Cin * esz;
   const size_t out_bytes = (size_t)K * op->Nt * c.Cout * esz;
-  {
-    const char* a = static_cast<const char*>(in);
-    const char* b = static_cast<const char*>(out);
-    if (a < b + out_bytes && b < a + in_bytes) return fail(FFTMV_EINVAL, "input and output overlap");
-  }
-  const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
   const size_t stage_in = in_dev ? 0 : align256(in_bytes);
   const size_t stage_out = out_dev ? 0 : align256(out_bytes);
   const size_t total = c.in_hat + c.out_hat + stage_in + stage_out;
@@ -393,6 +407,36 @@ int run_matvec(fftmv_op* op, int which, const void* in, void* out, int64_t K, in
   cudaError_t ef = cudaFreeAsync(ws, s);
   if (e != cudaSuccess) return cuda_fail(e, "matvec kernels");
   if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  return FFTMV_OK;
+}
+
+int run_matvec(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io, void* stream) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (K < 0) return fail(FFTMV_EINVAL, "K = %lld < 0", (long long)K);
+  if (io != FFTMV_IO_F64 && io != FFTMV_IO_F32) return fail(FFTMV_EINVAL, "io_dtype %d unknown", io);
+  if (K == 0) return FFTMV_OK;
+  if (!in || !out) return fail(FFTMV_EINVAL, "null input or output");
+  if (K > 65535) return fail(FFTMV_EUNSUPPORTED, "K = %lld exceeds 65535 right-hand sides per call", (long long)K);
+  DeviceGuard dg(op->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool fwd = which == FFTMV_FORWARD;
+  const int64_t Cin = fwd ? op->Nm : op->Nd, Cout = fwd ? op->Nd : op->Nm;
+  const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
+  const size_t in_rhs = (size_t)op->Nt * Cin * esz, out_rhs = (size_t)op->Nt * Cout * esz;
+  {
+    const char* a = static_cast<const char*>(in);
+    const char* b = static_cast<const char*>(out);
+    if (a < b + K * out_rhs && b < a + K * in_rhs) return fail(FFTMV_EINVAL, "input and output overlap");
+  }
+  const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
+  const int64_t kc = rhs_per_chunk(op, which, K, esz, !in_dev, !out_dev);
+  for (int64_t k0 = 0; k0 < K; k0 += kc) {
+    const int64_t k = K - k0 < kc ? K - k0 : kc;
+    rc = run_chunk(op, which, static_cast<const char*>(in) + k0 * in_rhs, static_cast<char*>(out) + k0 * out_rhs, k,
+                   io, s, in_dev, out_dev);
+    if (rc) return rc;
+  }
   // pageable host buffers: return once the result is in host memory; page-locked
   // ones stay stream ordered like device I/O
   if ((!in_dev && !is_pinned_host(in)) || (!out_dev && !is_pinned_host(out))) CUDA_TRY(cudaStreamSynchronize(s));
@@ -583,6 +627,13 @@ int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out)
   if (K < 0 || !out) return fail(FFTMV_EINVAL, "bad K or null output");
   const CallPlan c = plan_call(op, which, K);
   *out = c.in_hat + c.out_hat;
+  return FFTMV_OK;
+}
+
+int fftmv_set_scratch_limit(fftmv_op* op, size_t bytes) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  op->scratch_limit = bytes;
   return FFTMV_OK;
 }
 

@@ -73,7 +73,6 @@ struct KindF64 {
   static constexpr int P = 1;
   __device__ __forceinline__ static Acc zero() { return make_double2(0.0, 0.0); }
   __device__ __forceinline__ static Pack ldF(const Pack* p) { return __ldcs(p); }
-  __device__ __forceinline__ static Pack ldX(const Pack* p) { return __ldg(p); }
   // acc += f * x
   __device__ __forceinline__ static void mac_n(Acc& a, Pack f, Pack x) {
     a.x = fma(f.x, x.x, fma(-f.y, x.y, a.x));
@@ -98,7 +97,6 @@ struct KindDF {
   static constexpr int P = 1;
   __device__ __forceinline__ static Acc zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   __device__ __forceinline__ static Pack ldF(const Pack* p) { return __ldcs(p); }
-  __device__ __forceinline__ static Pack ldX(const Pack* p) { return __ldg(p); }
   // acc += (fr + i fi) * (xr + i xi) with s = +1, or conj(f) * x with s = -1,
   // each operand a hi/lo pair.  The four hi*hi products are split exactly by
   // TwoProd and their hi parts enter the accumulators through TwoSum; the
@@ -156,7 +154,6 @@ struct KindF32 {
   static constexpr int P = 2;
   __device__ __forceinline__ static Acc zero() { return make_float2(0.f, 0.f); }
   __device__ __forceinline__ static Pack ldF(const Pack* p) { return __ldcs(p); }
-  __device__ __forceinline__ static Pack ldX(const Pack* p) { return __ldg(p); }
   __device__ __forceinline__ static void mac_n(Acc& a, Pack f, Pack x) {
     a.x = fmaf(f.x, x.x, fmaf(-f.y, x.y, a.x));
     a.y = fmaf(f.x, x.y, fmaf(f.y, x.x, a.y));

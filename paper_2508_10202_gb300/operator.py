@@ -149,6 +149,10 @@ class Operator:
         L.check(L.lib().fftmv_workspace_bytes(self.handle, _WHICH[which], K, ctypes.byref(out)))
         return out.value
 
+    def set_scratch_limit(self, nbytes: int = 0) -> None:
+        """Bound the pool scratch of one launch sequence; larger K runs in chunks (0: 8 GiB)."""
+        L.check(L.lib().fftmv_set_scratch_limit(self.handle, int(nbytes)))
+
     # -- matvecs ------------------------------------------------------------
     def _apply(self, which: int, x, out, stream):
         n_in, n_out = (self.Nm, self.Nd) if which == L.FFTMV_FORWARD else (self.Nd, self.Nm)

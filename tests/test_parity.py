@@ -339,3 +339,29 @@ def test_shard_simulation_on_one_gpu(torch_cuda, pr, pc):
     assert oracle.rel_l2(x.cpu().numpy(), x_full) <= 1e-12
     assert oracle.rel_l2(y.cpu().numpy(), oracle.matvec_direct(Fcol, m[0])) <= 1e-12
     full.free()
+
+
+# --- large K in chunks within the scratch bound ------------------------------
+
+@pytest.mark.parametrize("prec,mode,fft_mode,tol", [("sssss", "bf16x2", "native", 1e-6),
+                                                    ("ddddd", "f64x2f32", "f64x2f32", 1e-13)])
+def test_scratch_limit_chunks_rhs(torch_cuda, prec, mode, fft_mode, tol):
+    torch = torch_cuda
+    Fcol, m, d = make_case(48, 7, 150, K=150, seed=31)
+    op = gpu_op(torch, Fcol)
+    for w in ("F", "F*"):
+        op.set_precision(w, prec, mode, fft_mode)
+    io = np.float32 if prec == "sssss" else np.float64
+    mt, dt = torch.from_numpy(m.astype(io)).cuda(), torch.from_numpy(d.astype(io)).cuda()
+    y_all, x_all = op.matvec(mt).cpu().numpy(), op.rmatvec(dt).cpu().numpy()
+    # a bound that admits one 64-RHS chunk at most: 3 launch sequences
+    need = max(op.workspace_bytes("F", 64), op.workspace_bytes("F*", 64))
+    op.set_scratch_limit(need)
+    y_ch, x_ch = op.matvec(mt).cpu().numpy(), op.rmatvec(dt).cpu().numpy()
+    assert oracle.rel_l2(y_ch, y_all) <= tol and oracle.rel_l2(x_ch, x_all) <= tol
+    # host I/O through the chunks (pageable: the call returns with the result)
+    y_host = op.matvec(m.astype(io))
+    assert oracle.rel_l2(y_host, y_all) <= tol
+    assert oracle.rel_l2(y_all, oracle.matvec_direct(Fcol, m.astype(io).astype(np.float64))) <= (TOL64 if prec == "ddddd" else TOL32)
+    op.set_scratch_limit(0)
+    op.free()
