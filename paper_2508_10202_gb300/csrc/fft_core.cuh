@@ -562,6 +562,15 @@ __host__ __device__ constexpr int fft_pairs(int L) {
   while (np > 1 && (size_t)np * L * sizeof(typename Ar<P>::C) > kFftTileBytes) np /= 2;
   return np;
 }
+// the forward FFT that writes tensor-core B planes in FP32 takes twice the
+// channels (up to 128 KB, one CTA per SM): every thread then stores whole
+// 32-byte sectors of a B row instead of halves
+template <typename P>
+__host__ __device__ constexpr int fft_pairs_tc(int L) {
+  int np = 8;
+  while (np > 1 && (size_t)np * L * sizeof(typename Ar<P>::C) > 2 * kFftTileBytes) np /= 2;
+  return std::is_same<P, float>::value ? np : fft_pairs<P>(L);
+}
 template <typename P>
 __host__ __device__ constexpr int fft_nthreads(int np, int L, int e = kFftE<P>) {
   const int t = ((np * L + e - 1) / e + 31) / 32 * 32;
@@ -612,15 +621,16 @@ template <typename P>
 __host__ __device__ constexpr int fft_elems(int L) {
   return (std::is_same<P, float>::value && (L == 2000 || L == 1000)) ? 25 : kFftE<P>;
 }
-// launch bounds of the length-L kernel: 25-element threads get up to 102
-// registers (320 threads, two CTAs per SM); the others 64
+// launch bounds of the length-L kernel: its exact thread count; 25-element
+// threads get up to 65536 / (threads * CTAs per SM) registers (about 100),
+// the others 64
 template <typename P>
-__host__ __device__ constexpr int fft_bound_threads(int LC) {
-  return LC > 0 && fft_elems<P>(LC) == 25 ? 320 : 1024;
+__host__ __device__ constexpr int fft_bound_threads(int NP, int LC) {
+  return LC > 0 && fft_elems<P>(LC) == 25 ? fft_nthreads<P>(NP, LC, 25) : 1024;
 }
 template <typename P>
-__host__ __device__ constexpr int fft_bound_blocks(int LC) {
-  return LC > 0 && fft_elems<P>(LC) == 25 ? 2 : 1;
+__host__ __device__ constexpr int fft_bound_blocks(int NP, int LC) {
+  return LC > 0 && fft_elems<P>(LC) == 25 ? (fft_bound_threads<P>(NP, LC) <= 320 ? 2 : 1) : 1;
 }
 __host__ __device__ constexpr unsigned cmagic(int ns) {
   return ns > 1 ? (unsigned)((((unsigned long long)1 << 32) + (unsigned long long)ns - 1) / (unsigned long long)ns) : 0u;
@@ -704,7 +714,7 @@ __device__ __forceinline__ typename Ar<P>::C load_cx(const void* X, int64_t i, i
 // other passes run in place in shared memory, then the real/imaginary split
 // writes the spectra.
 template <typename Tin, typename P, int NP, int LC>
-__global__ void __launch_bounds__(fft_bound_threads<P>(LC), fft_bound_blocks<P>(LC)) rfft_fwd_kernel(FwdDesc d) {
+__global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks<P>(NP, LC)) rfft_fwd_kernel(FwdDesc d) {
   using A = Ar<P>;
   using C = typename A::C;
   using R = typename A::R;
@@ -848,7 +858,7 @@ __device__ __forceinline__ void store_real(void* y, int64_t i, typename Ar<P>::R
 // place, and the last pass writes t < Nt straight to HBM (1/L scale, unpad and
 // output cast fused).
 template <typename P, typename Tout, int NP, int LC>
-__global__ void __launch_bounds__(fft_bound_threads<P>(LC), fft_bound_blocks<P>(LC)) irfft_inv_kernel(InvDesc d) {
+__global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks<P>(NP, LC)) irfft_inv_kernel(InvDesc d) {
   using A = Ar<P>;
   using C = typename A::C;
   constexpr int E = LC > 0 ? fft_elems<P>(LC) : kFftE<P>;
@@ -946,8 +956,10 @@ cudaError_t inv_launch_np(const InvDesc& d, cudaStream_t s) {
 template <typename Tin, typename P>
 cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
   switch (d.plan.L) {
-#define FFTMV_CASE(LL) \
-  case LL: return fwd_launch_np<Tin, P, fft_pairs<P>(LL), LL>(d, s);
+#define FFTMV_CASE(LL)                                                                         \
+  case LL:                                                                                      \
+    if (d.fmt == FMT_TC) return fwd_launch_np<Tin, P, fft_pairs_tc<P>(LL), LL>(d, s); \
+    return fwd_launch_np<Tin, P, fft_pairs<P>(LL), LL>(d, s);
     FFTMV_FIXED_LENGTHS(FFTMV_CASE)
 #undef FFTMV_CASE
     default: break;
