@@ -656,11 +656,14 @@ __device__ __forceinline__ void cpasses(int T, const typename Ar<P>::C* __restri
 // --- loads and stores with the phase casts --------------------------------
 
 template <typename P, typename Tin>
-__device__ __forceinline__ typename Ar<P>::R load_real(const void* p, int64_t i, bool pad_single) {
-  const Tin x = __ldg(static_cast<const Tin*>(p) + i);
+__device__ __forceinline__ typename Ar<P>::R cvt_real(Tin x, bool pad_single) {
   if (pad_single) return Ar<P>::from_f((float)x);
   if constexpr (sizeof(Tin) == 8) return Ar<P>::from_d((double)x);
   else return Ar<P>::from_f((float)x);
+}
+template <typename P, typename Tin>
+__device__ __forceinline__ typename Ar<P>::R load_real(const void* p, int64_t i, bool pad_single) {
+  return cvt_real<P, Tin>(__ldg(static_cast<const Tin*>(p) + i), pad_single);
 }
 
 // store one complex value (re, im) of precision P into format fmt
@@ -737,6 +740,11 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
     const int c = c0 + 2 * p;
     if (t >= d.Nt || c >= d.cols) return zero;
     const int64_t o = xo + t * d.x_ld_t + c;
+    if (d.pair_ok && c + 1 < d.cols) {   // both channels in one 8- or 16-byte load
+      using V = typename std::conditional<sizeof(Tin) == 4, float2, double2>::type;
+      const V v = __ldg(reinterpret_cast<const V*>(static_cast<const Tin*>(d.x) + o));
+      return A::mk(cvt_real<P, Tin>(v.x, d.pad_single), cvt_real<P, Tin>(v.y, d.pad_single));
+    }
     const R a = load_real<P, Tin>(d.x, o, d.pad_single);
     const R bb = c + 1 < d.cols ? load_real<P, Tin>(d.x, o + 1, d.pad_single) : A::zero();
     return A::mk(a, bb);
@@ -884,8 +892,14 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
       const int w = i / NP, p = i - w * NP;
       const int ca = c0 + 2 * p, cb = ca + 1;
       const bool in = i < Nf * NP;
-      a[u] = in && ca < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt) : zero;
-      bb[u] = in && cb < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : zero;
+      if (in && d.pair_ok && cb < d.cols) {   // FP32 spectra of both channels in one 16-byte load
+        const float4 v = __ldg(reinterpret_cast<const float4*>(static_cast<const float2*>(d.X) + Xo + w * d.X_ld_w + ca));
+        a[u] = A::mk(A::from_f(v.x), A::from_f(v.y));
+        bb[u] = A::mk(A::from_f(v.z), A::from_f(v.w));
+      } else {
+        a[u] = in && ca < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt) : zero;
+        bb[u] = in && cb < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : zero;
+      }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {

@@ -260,6 +260,10 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   f.X_ld_b = op->Nf * c.in_ld;
   f.fmt = c.in_fmt;
   f.pad_single = p.pad == FFTMV_F32;
+  {
+    const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
+    f.pair_ok = (reinterpret_cast<uintptr_t>(x) % (2 * esz) == 0) && f.x_ld_t % 2 == 0 && f.x_ld_b % 2 == 0;
+  }
   cudaError_t e = cudaSuccess;
   if (c.kind == GEMV_TC) {
     const TcShape t = tc_shape((int)K);
@@ -319,6 +323,8 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     v.y_ld_b = op->Nt * c.Cout;
     v.in_fmt = c.out_fmt;
     v.unpad_single = p.unpad == FFTMV_F32;
+    v.pair_ok = c.out_fmt == FMT_C64 && reinterpret_cast<uintptr_t>(out_hat) % 16 == 0 && v.X_ld_w % 2 == 0 &&
+                v.X_ld_b % 2 == 0;
     v.inv_L = 1.0 / (double)op->L;
     v.inv_L_hi = (float)v.inv_L;
     v.inv_L_lo = (float)(v.inv_L - (double)v.inv_L_hi);

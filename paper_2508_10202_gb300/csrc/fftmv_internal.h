@@ -64,6 +64,7 @@ struct FwdDesc {
   int fmt;                 // CFmt of X
   int pad_single;          // round the loaded input to FP32 (pad phase in FP32)
   int tc_KC, tc_N, tc_J;   // FMT_TC: right-hand sides per chunk, rows per chunk, rows per plane
+  int pair_ok;             // x and its strides allow loading channels (2q, 2q+1) as one vector
 };
 
 // Inverse real FFT of Hermitian half spectra followed by unpad (phases 4-5 fused).
@@ -80,6 +81,7 @@ struct InvDesc {
   int64_t y_ld_t, y_ld_b;  // element strides
   int in_fmt;              // FMT_C128, FMT_C64 or FMT_DF
   int unpad_single;        // round the result to FP32 before the output cast
+  int pair_ok;             // FMT_C64 X and its strides allow loading channels (2q, 2q+1) as one float4
   double inv_L;            // 1/L in FP64 and as an FP32 hi/lo pair
   float inv_L_hi, inv_L_lo;
 };
