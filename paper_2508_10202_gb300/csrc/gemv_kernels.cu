@@ -23,6 +23,8 @@
 //            GEMV; the FP32 pipe can.
 //  GEMV_F32: FP32 F-hat (8 B per entry), FP32 FMA.
 
+#include <type_traits>
+
 #include "fftmv_internal.h"
 #include "pipe.cuh"
 
@@ -397,7 +399,12 @@ __global__ void convert_f32_kernel(const double2* __restrict__ in, float2* __res
   }
 }
 
-constexpr int kNR = 8, kNW = 8, kNS = 3;     // N: rows per CTA, consumer warps, pipeline stages
+// N, one right-hand side: rows per CTA, consumer warps, pipeline stages.
+// Double-float takes 4 rows and 4 consumer warps (55 KB of stages, four CTAs
+// per SM: 2.30 ms against 2.45 ms for 8 x 8 at the paper shape); FP32 and FP64
+// keep 8 rows and 8 warps, their best.
+constexpr int kNR = 8, kNW = 8, kNS = 3;
+constexpr int kNR_DF = 4, kNW_DF = 4;
 constexpr int kHV = 2, kHT = 256, kHU = 4;   // H: packs per thread, threads, rows in flight
 
 template <class Kd, int R, int KB, int NCW, int STAGES>
@@ -414,7 +421,8 @@ cudaError_t run_n_cfg(const GemvDesc& d, cudaStream_t s) {
 
 template <class Kd>
 cudaError_t run_n(const GemvDesc& d, cudaStream_t s) {
-  return run_n_cfg<Kd, kNR, 1, kNW, kNS>(d, s);
+  if constexpr (std::is_same<Kd, KindDF>::value) return run_n_cfg<Kd, kNR_DF, 1, kNW_DF, kNS>(d, s);
+  else return run_n_cfg<Kd, kNR, 1, kNW, kNS>(d, s);
 }
 
 template <class Kd, int KB>
