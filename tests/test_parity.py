@@ -365,3 +365,26 @@ def test_scratch_limit_chunks_rhs(torch_cuda, prec, mode, fft_mode, tol):
     assert oracle.rel_l2(y_all, oracle.matvec_direct(Fcol, m.astype(io).astype(np.float64))) <= (TOL64 if prec == "ddddd" else TOL32)
     op.set_scratch_limit(0)
     op.free()
+
+
+# --- the longest FFT (L = 8192: one signal per CTA, 1024 threads) ------------
+
+@pytest.mark.parametrize("prec,mode,fft_mode", [("ddddd", "native", "native"), ("ddddd", "f64x2f32", "f64x2f32"),
+                                                ("sssss", "native", "native")])
+def test_maximum_length(torch_cuda, prec, mode, fft_mode):
+    torch = torch_cuda
+    from paper_2508_10202_gb300 import FftmvError, Operator
+    Nt, Nd, Nm = 4096, 2, 5
+    Fcol, m, d = make_case(Nt, Nd, Nm, K=2, seed=77, decay=300.0)
+    op = gpu_op(torch, Fcol)
+    assert op.L == 8192
+    for w in ("F", "F*"):
+        op.set_precision(w, prec, mode, fft_mode)
+    y, x = run_both(torch, op, m, d)
+    tol = TOL64 if prec == "ddddd" else TOL32
+    assert oracle.rel_l2(y, oracle.matvec_direct(Fcol, m)) <= tol
+    assert oracle.rel_l2(x, oracle.rmatvec_direct(Fcol, d)) <= tol
+    op.free()
+    # one block more needs a longer transform than one CTA holds: refused at creation
+    with pytest.raises(FftmvError, match="exceeds"):
+        Operator(torch.zeros((Nt + 1, 1, 1), dtype=torch.float64, device="cuda"))
