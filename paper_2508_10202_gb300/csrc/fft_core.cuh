@@ -562,15 +562,6 @@ __host__ __device__ constexpr int fft_pairs(int L) {
   while (np > 1 && (size_t)np * L * sizeof(typename Ar<P>::C) > kFftTileBytes) np /= 2;
   return np;
 }
-// the forward FFT that writes tensor-core B planes in FP32 takes twice the
-// channels (up to 128 KB, one CTA per SM): every thread then stores whole
-// 32-byte sectors of a B row instead of halves
-template <typename P>
-__host__ __device__ constexpr int fft_pairs_tc(int L) {
-  int np = 8;
-  while (np > 1 && (size_t)np * L * sizeof(typename Ar<P>::C) > 2 * kFftTileBytes) np /= 2;
-  return std::is_same<P, float>::value ? np : fft_pairs<P>(L);
-}
 template <typename P>
 __host__ __device__ constexpr int fft_nthreads(int np, int L, int e = kFftE<P>) {
   const int t = ((np * L + e - 1) / e + 31) / 32 * 32;
@@ -774,9 +765,10 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
     }
   };
   if (d.fmt == FMT_TC) {
-    // bf16 hi/lo B planes [2][J][ldb/64][Nf][64] (ldb = out_cols): a thread
-    // takes one frequency and G adjacent channels, and writes them as one
-    // 2G-byte run into each of the four rows (Re, Im) x (hi, lo)
+    // bf16 hi/lo B planes [2][J][ldb/g][Nf][g] (ldb = out_cols, g = 2^tc_group_log2):
+    // a thread takes one frequency and G adjacent channels, and writes them as
+    // one 2G-byte run into each of the four rows (Re, Im) x (hi, lo);
+    // consecutive threads take consecutive frequencies (adjacent runs for g = 8)
     constexpr int G = NCH < 8 ? NCH : 8;
     constexpr int NG = NCH / G;
     using Vec = typename std::conditional<G == 8, uint4, typename std::conditional<G == 4, uint2, uint32_t>::type>::type;
@@ -832,7 +824,8 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
         h[2][u] = __float2bfloat16(fi);
         h[3][u] = __float2bfloat16(fi - __bfloat162float(h[2][u]));
       }
-      const int64_t off = ((int64_t)(c >> 6) * Nf + w) * 64 + (c & 63);
+      const int sh = d.tc_group_log2;
+      const int64_t off = (((int64_t)(c >> sh) * Nf + w) << sh) + (c & ((1 << sh) - 1));
       *reinterpret_cast<Vec*>(B + jr * row_el + off) = *reinterpret_cast<const Vec*>(h[0]);
       *reinterpret_cast<Vec*>(B + plane_el + jr * row_el + off) = *reinterpret_cast<const Vec*>(h[1]);
       *reinterpret_cast<Vec*>(B + ji * row_el + off) = *reinterpret_cast<const Vec*>(h[2]);
@@ -970,10 +963,8 @@ cudaError_t inv_launch_np(const InvDesc& d, cudaStream_t s) {
 template <typename Tin, typename P>
 cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
   switch (d.plan.L) {
-#define FFTMV_CASE(LL)                                                                         \
-  case LL:                                                                                      \
-    if (d.fmt == FMT_TC) return fwd_launch_np<Tin, P, fft_pairs_tc<P>(LL), LL>(d, s); \
-    return fwd_launch_np<Tin, P, fft_pairs<P>(LL), LL>(d, s);
+#define FFTMV_CASE(LL) \
+  case LL: return fwd_launch_np<Tin, P, fft_pairs<P>(LL), LL>(d, s);
     FFTMV_FIXED_LENGTHS(FFTMV_CASE)
 #undef FFTMV_CASE
     default: break;

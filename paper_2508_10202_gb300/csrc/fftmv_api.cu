@@ -223,7 +223,7 @@ CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
   c.Cout = fwd ? op->Nd : op->Nm;
   c.in_ld = fwd ? op->ldn : op->Nd;
   c.out_ld = fwd ? op->Nd : op->ldn;
-  if (c.kind == GEMV_TC) {  // B operand planes [2][J][ldb/64][Nf][64] bf16
+  if (c.kind == GEMV_TC) {  // B operand planes (TcDesc), 2 J ldb Nf bf16
     c.in_ld = tc_ldb((int)c.Cin);
     c.in_hat = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld));
   } else {
@@ -270,6 +270,7 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     f.tc_KC = t.KC;
     f.tc_N = t.N;
     f.tc_J = t.J;
+    f.tc_group_log2 = fwd ? 3 : 6;
     // B rows no right-hand side fills (chunk padding, a short last chunk) must read as zero
     if (2 * t.KC < t.N || (int)K % t.KC != 0)
       e = cudaMemsetAsync(in_hat, 0, tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld), s);

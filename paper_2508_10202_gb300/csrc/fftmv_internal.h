@@ -14,7 +14,7 @@ enum CFmt : int {
   FMT_C64 = 1,   // float2 (re, im)
   FMT_DF = 2,    // float4 (re_hi, im_hi, re_lo, im_lo): value = hi + lo, |lo| <= ulp(hi)/2
   FMT_TC = 3,    // spectra for the tensor cores, written straight into the bf16 B operand
-                 // planes [hi, lo][J][ldb / 64][Nf][64] (TcShape, TcDesc)
+                 // planes (TcShape, TcDesc)
 };
 
 // Arithmetic used by the per-frequency block matvec (phase 3).
@@ -64,6 +64,7 @@ struct FwdDesc {
   int fmt;                 // CFmt of X
   int pad_single;          // round the loaded input to FP32 (pad phase in FP32)
   int tc_KC, tc_N, tc_J;   // FMT_TC: right-hand sides per chunk, rows per chunk, rows per plane
+  int tc_group_log2;       // FMT_TC: log2 of the channels per contiguous run of a B row, 3 (F) or 6 (F*)
   int pair_ok;             // x and its strides allow loading channels (2q, 2q+1) as one vector
 };
 
@@ -109,9 +110,10 @@ TcShape tc_shape(int K);
 
 struct TcDesc {
   const void* A;           // bf16 planes [Nf][4][Nd][ldn] (Re hi, Re lo, Im hi, Im lo)
-  const void* B;           // bf16 planes [2][J][ldb / 64][Nf][64]: entry (plane, row j, frequency w,
-                           // contraction index k) at (((plane J + j) ldb/64 + k/64) Nf + w) 64 + k%64;
-                           // k < ldb = the contraction length (Nm for F, Nd for F*) rounded up to 64
+  const void* B;           // bf16 planes; entry (plane, row j, frequency w, contraction index k),
+                           // k < ldb = the contraction length (Nm for F, Nd for F*) rounded up to 64, at
+                           //   F:  (((plane J + j) ldb/8 + k/8) Nf + w) 8 + k%8      ([2][J][ldb/8][Nf][8])
+                           //   F*: (((plane J + j) ldb/64 + k/64) Nf + w) 64 + k%64  ([2][J][ldb/64][Nf][64])
   void* y;                 // FMT_C64 [K][Nf][Nd] (F) or [K][Nf][ldn] (F*)
   int Nf, Nd, Nm, ldn, ldb, K;
   int adjoint;             // 0: F (contract over n), 1: F* (contract over r, A read transposed)

@@ -84,6 +84,18 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(const void* smem) {
   return d;
 }
 
+// shared-memory matrix descriptor: K-major, no swizzle.  8-row x 16-byte core
+// matrices (128 contiguous bytes each): the next core matrix along K is 128 B
+// on (leading byte offset), the next 8-row group 1024 B on (stride byte offset).
+__device__ __forceinline__ uint64_t umma_desc_kmajor_plain(const void* smem) {
+  const uint64_t addr = smem_u32(smem);
+  uint64_t d = (addr & 0x3FFFFull) >> 4;
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;                   // descriptor version (sm_100); layout 0: no swizzle
+  return d;
+}
+
 // shared-memory matrix descriptor: MN-major, 128-byte swizzle.  A 128 x 64
 // tile is two 64-wide MN halves 8 KB apart (leading byte offset), each 64 K
 // rows of 128 bytes; K groups of 8 rows are 1024 B apart (stride byte offset).
@@ -149,6 +161,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 struct TcArgs {
   int Nf, M, K, KC, N, nkb;  // M: output rows (Nd for F, Nm for F*)
+  int J;                     // B rows per plane
   int nch, nmt;              // right-hand-side chunks and 128-row M tiles per frequency
   int64_t y_ld_b, y_ld_w;    // complex elements between right-hand sides / frequencies of y
   float2* y;                 // [K][Nf][rows] (FMT_C64)
@@ -232,7 +245,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               tma_load_4d(st + p * a_plane, &mapA, kb * TC_BK, m0, p, w, &full[s]);
             }
           }
-          for (int p = 0; p < 2; ++p) tma_load_5d(st + 4 * a_plane + p * b_plane, &mapB, 0, w, kb, ch * N, p, &full[s]);
+          for (int p = 0; p < 2; ++p) {
+            if constexpr (H)   // [2][J][ldb/64][Nf][64]: N rows of 64 indices, 128-byte swizzle
+              tma_load_5d(st + 4 * a_plane + p * b_plane, &mapB, 0, w, kb, ch * N, p, &full[s]);
+            else               // [2][J][ldb/8][Nf][8]: 8 x 8 x 8 x N/8 core-matrix box
+              tma_load_5d(st + 4 * a_plane + p * b_plane, &mapB, 0, 0, kb * (TC_BK / 8), (p * a.J + ch * N) / 8, w,
+                          &full[s]);
+          }
         }
       }
       // no copy may still be in flight when the CTA exits
@@ -269,8 +288,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint64_t frl = (H ? umma_desc_mn_sw128(st + 1 * a_plane) : umma_desc_sw128(st + 1 * a_plane)) + ak;
             const uint64_t fih = (H ? umma_desc_mn_sw128(st + 2 * a_plane) : umma_desc_sw128(st + 2 * a_plane)) + ak;
             const uint64_t fil = (H ? umma_desc_mn_sw128(st + 3 * a_plane) : umma_desc_sw128(st + 3 * a_plane)) + ak;
-            const uint64_t bh = umma_desc_sw128(st + 4 * a_plane) + 2 * ks;
-            const uint64_t bl = umma_desc_sw128(st + 4 * a_plane + b_plane) + 2 * ks;
+            // B: F* 32 B per 16 K inside the swizzled row; F two core matrices (256 B)
+            const uint64_t bk = H ? 2 * ks : (uint64_t)(256 >> 4) * ks;
+            const uint64_t bh = (H ? umma_desc_sw128(st + 4 * a_plane) : umma_desc_kmajor_plain(st + 4 * a_plane)) + bk;
+            const uint64_t bl =
+                (H ? umma_desc_sw128(st + 4 * a_plane + b_plane) : umma_desc_kmajor_plain(st + 4 * a_plane + b_plane)) + bk;
             const uint32_t acc = !(first && ks == 0);
             umma_bf16(acc1, frh, bh, idesc, acc);
             umma_bf16(acc1, frh, bl, idesc, 1);
@@ -400,20 +422,37 @@ cudaError_t make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// B operand map over bf16 planes [2][J][ldb / 64][Nf][64] (see TcDesc): dims
-// {64, Nf, ldb / 64, J, 2}, box {64, 1, 1, N, 1}.  The box lands in shared
-// memory as N rows of 64 contraction indices (128 bytes): the same K-major
-// 128-byte-swizzled tile a {64, N} box of a row-major plane gives.
-cudaError_t make_map_b(CUtensorMap* map, const void* base, uint64_t ldb, uint64_t J, uint64_t Nf, uint32_t box_rows) {
+// B operand maps.  F (large B, written by the costly FFT over Nm channels):
+// planes [2][J][ldb/8][Nf][8] folded into 2J rows; dims {8 channels, 8 rows,
+// ldb/8 channel groups, 2J/8 row groups, Nf}, box {8, 8, 8, N/8, 1}, no
+// swizzle: the box lands as the K-major core-matrix layout (8 rows x 16 bytes
+// per core matrix, K-neighbours 128 B apart, 8-row groups 1024 B apart) that
+// umma_desc_kmajor_plain reads, and the FFT writes 16-byte runs that are
+// adjacent over frequencies.  F* (small B, re-read by every M tile): planes
+// [2][J][ldb/64][Nf][64]; dims {64, Nf, ldb/64, J, 2}, box {64, 1, 1, N, 1},
+// 128-byte swizzle: N rows of 64 indices, one 128-byte request per row.
+cudaError_t make_map_b(CUtensorMap* map, const void* base, uint64_t ldb, uint64_t J, uint64_t Nf, uint32_t box_rows,
+                       bool adjoint) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  const cuuint64_t dims[5] = {64, Nf, ldb / 64, J, 2};
-  const cuuint64_t strides[4] = {128, Nf * 128, ldb * Nf * 2, J * ldb * Nf * 2};
-  const cuuint32_t box[5] = {TC_BK, 1, 1, box_rows, 1};
+  CUresult r;
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (adjoint) {
+    const cuuint64_t dims[5] = {64, Nf, ldb / 64, J, 2};
+    const cuuint64_t strides[4] = {128, Nf * 128, ldb * Nf * 2, J * ldb * Nf * 2};
+    const cuuint32_t box[5] = {TC_BK, 1, 1, box_rows, 1};
+    r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    const uint64_t row = (ldb / 8) * Nf * 16;   // bytes per B row
+    const cuuint64_t dims[5] = {8, 8, ldb / 8, 2 * J / 8, Nf};
+    const cuuint64_t strides[4] = {row, Nf * 16, 8 * row, 16};
+    const cuuint32_t box[5] = {8, 8, TC_BK / 8, box_rows / 8, 1};
+    r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -453,7 +492,7 @@ cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s) {
   CUtensorMap mapA, mapB;
   cudaError_t e = make_map(&mapA, d.A, (uint64_t)d.ldn, (uint64_t)d.Nd, 4, (uint64_t)d.Nf, H ? 64 : TC_M);
   if (e != cudaSuccess) return e;
-  e = make_map_b(&mapB, d.B, (uint64_t)d.ldb, (uint64_t)t.J, (uint64_t)d.Nf, (uint32_t)t.N);
+  e = make_map_b(&mapB, d.B, (uint64_t)d.ldb, (uint64_t)t.J, (uint64_t)d.Nf, (uint32_t)t.N, H);
   if (e != cudaSuccess) return e;
   TcArgs a{};
   a.Nf = d.Nf;
@@ -463,6 +502,7 @@ cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s) {
   a.N = t.N;
   a.nkb = d.ldb / TC_BK;
   a.nch = t.nch;
+  a.J = t.J;
   a.nmt = (a.M + TC_M - 1) / TC_M;
   a.y_ld_b = d.y_ld_b;
   a.y_ld_w = H ? d.ldn : d.Nd;
