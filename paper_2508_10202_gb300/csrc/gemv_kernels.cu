@@ -428,11 +428,12 @@ cudaError_t run_n(const GemvDesc& d, cudaStream_t s) {
 template <class Kd, int KB>
 cudaError_t run_h_kb(const GemvDesc& d, cudaStream_t s) {
   // (packs per thread, threads): double-float, one RHS: 4 x 128 (2.33 ms against
-  // 2.36 for 2 x 256 at the paper shape); FP32, eight RHS: 2 x 512 (1.85 against
-  // 2.64 ms); otherwise 2 x 256
+  // 2.36 for 2 x 256 at the paper shape); double-float, 4 RHS: 1 x 256 (6.5 against
+  // 7.0 ms); FP32, eight RHS: 2 x 512 (1.85 against 2.64 ms); otherwise 2 x 256
   constexpr bool df1 = std::is_same<Kd, KindDF>::value && KB == 1;
   constexpr bool f8 = std::is_same<Kd, KindF32>::value && KB == 8;
-  constexpr int V = df1 ? 4 : kHV, T = df1 ? 128 : f8 ? 512 : kHT;
+  constexpr bool dfk = std::is_same<Kd, KindDF>::value && KB > 1;   // double-float, several RHS: 1 x 256
+  constexpr int V = df1 ? 4 : dfk ? 1 : kHV, T = df1 ? 128 : f8 ? 512 : kHT;
   const int ldp = d.ldn / Kd::P;
   dim3 grid((ldp + T * V - 1) / (T * V), d.Nf, (d.K + KB - 1) / KB);
   const size_t smem = (size_t)KB * d.Nd * sizeof(typename Kd::Elem);
@@ -480,7 +481,8 @@ cudaError_t launch_gemv_n(int kind, const GemvDesc& d, cudaStream_t s) {
     // one right-hand side: 8 rows per CTA; several: every F-hat pack feeds
     // KB of them (FP64 stays at one: its FMA rate, not HBM, bounds it)
     case GEMV_F64: return run_n<KindF64>(d, s);
-    case GEMV_DF: return d.K == 1 ? run_n<KindDF>(d, s) : run_n_cfg<KindDF, 2, 4, 4, 3>(d, s);
+    // double-float, several RHS: 4 rows x 4 RHS, 4 warps (4 RHS: 8.4 ms against 9.2 for 2 rows)
+    case GEMV_DF: return d.K == 1 ? run_n<KindDF>(d, s) : run_n_cfg<KindDF, 4, 4, 4, 3>(d, s);
     // FP32, several RHS: 8 rows x 8 RHS, 4 consumer warps, 2 stages (8 RHS at the
     // paper shape: 2.14 ms against 2.89 for 4 rows x 8 RHS with 3 stages)
     default: return d.K == 1 ? run_n<KindF32>(d, s) : run_n_cfg<KindF32, 8, 8, 4, 2>(d, s);
