@@ -106,3 +106,29 @@ def test_tensor_core_matches_cuda_core_fp32(torch_cuda):
     b = op.matvec(m).cpu().numpy()
     assert oracle.rel_l2(b, a) <= 2 * TOL
     op.free()
+
+
+@pytest.mark.parametrize("which", ["F", "F*"])
+def test_tensor_core_many_tiles_per_cta(torch_cuda, which):
+    # F: 301 frequencies (two tiles for some of the 152 persistent CTAs); F*: 301 x 5
+    # M tiles (about ten each): the pipeline phases carry across tiles.  Checked
+    # against the oracle's FFT path (pinned to the definition in test_oracle.py).
+    torch = torch_cuda
+    from paper_2508_10202_gb300 import Operator
+    Nt, Nd, Nm, K = 300, 100, 640, 64
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=41)
+    op = Operator(torch.from_numpy(Fcol).cuda())
+    op.set_precision(which, "sssss", "bf16x2")
+    if which == "F":
+        x = synth.vectors(synth.TAG_M, Nt, Nm, k=K, seed=41)
+        got = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+        ref = oracle.matvec_fft(Fcol, x)
+    else:
+        x = synth.vectors(synth.TAG_D, Nt, Nd, k=K, seed=41)
+        got = op.rmatvec(torch.from_numpy(x).cuda()).cpu().numpy()
+        ref = oracle.rmatvec_fft(Fcol, x)
+    assert oracle.rel_l2(got, ref) <= TOL
+    for b in (0, 31, 63):
+        assert oracle.rel_l2(got[b], ref[b]) <= 3 * TOL
+    assert op.device_status() == 0
+    op.free()
