@@ -40,8 +40,8 @@
  * Threads and streams.  Different operators may be used from different
  * threads at once.  Calls on one operator may run on different streams at the
  * same time (each call takes its scratch from a stream-ordered pool), except
- * that fftmv_set_precision and fftmv_free must not overlap other calls on the
- * same operator.
+ * that fftmv_set_precision, fftmv_set_scratch_limit and fftmv_free must not
+ * overlap other calls on the same operator.
  */
 #ifndef FFTMV_H
 #define FFTMV_H
