@@ -299,9 +299,11 @@ def time_variant(torch, op, mt, dt, yt, xt, stream, pf, pa, steps: int) -> dict:
             "phase_ms_F": [v / nf for v in tf], "phase_ms_Fstar": [v / na for v in ta]}
 
 
-def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: int = 64, steps: int = 10) -> dict:
+def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: int = 64, steps: int = 10,
+                    mode: str = "bf16x2") -> dict:
     """K right-hand sides through F (or F*) at once: FP32 phases, block matvec on
-    the tensor cores with bf16 hi/lo F-hat, the multi-RHS workload."""
+    the tensor cores with F-hat and the spectra split into bf16 (or FP16, scaled)
+    hi + lo parts, the multi-RHS workload."""
     import numpy as np
 
     import synth
@@ -311,7 +313,7 @@ def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: in
     x = synth.vectors(synth.TAG_M if fwd else synth.TAG_D, Nt, n_in, k=K, seed=7, dtype=np.float32)
     xt = torch.from_numpy(x).to(dev)
     yt = torch.empty((K, Nt, n_out), dtype=torch.float32, device=dev)
-    op.set_precision(which, "sssss", "bf16x2")
+    op.set_precision(which, "sssss", mode)
     call = op.matvec if fwd else op.rmatvec
     for _ in range(2):
         call(xt, out=yt, stream=stream)
@@ -352,7 +354,8 @@ def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: in
     hbm, _ = peaks
     bf16_peak = load_tensor_peak()
     tb = a_bytes + io_bytes
-    return {"which": which, "K": K, "prec": "sssss/bf16x2 (tcgen05, bf16 hi+lo, FP32 accumulate)", "ms_call": ms,
+    desc = ("bf16 hi+lo" if mode == "bf16x2" else "FP16 hi+lo, power-of-two scale per frequency and per RHS")
+    return {"which": which, "K": K, "prec": f"sssss/{mode} (tcgen05, {desc}, FP32 accumulate)", "ms_call": ms,
             "matvec_s": K / (ms * 1e-3), "phase_ms": ph, "rel_err_sampled": err,
             "tc_kernel": {"hbm_bytes": tb, "achieved_GBs": tb / tc_s / 1e9,
                           "hbm_frac": tb / tc_s / 1e9 / hbm,
@@ -638,6 +641,8 @@ def main(args) -> None:
     multi = None
     if rank == 0 and not args.no_multi:
         multi = {w: bench_multi_rhs(torch, op, Fcol, dev, stream, (peak, peak_kind), which=w) for w in ("F", "F*")}
+        for w in ("F", "F*"):
+            multi[w + " f16x2"] = bench_multi_rhs(torch, op, Fcol, dev, stream, (peak, peak_kind), which=w, mode="f16x2")
 
     hess = None
     if rank == 0 and not args.no_multi:

@@ -78,8 +78,19 @@ typedef enum { FFTMV_F64 = 0, FFTMV_F32 = 1 } fftmv_phase_prec;
  *              tensor cores (tcgen05): F-hat and the transformed inputs
  *              split into bfloat16 hi + lo parts (about 16 significant bits),
  *              hi*hi + hi*lo + lo*hi accumulated in FP32.  Pays off once K is
- *              large (tens of right-hand sides); its error is at FP32 level. */
-typedef enum { FFTMV_GEMV_NATIVE = 0, FFTMV_GEMV_F64X2F32 = 1, FFTMV_GEMV_BF16X2 = 2 } fftmv_gemv_mode;
+ *              large (tens of right-hand sides); its error is at FP32 level.
+ *   F16X2    : gemv=F32 only.  As BF16X2 with FP16 hi + lo parts (about 22
+ *              significant bits): F-hat scaled by a power of two per
+ *              frequency, the transformed inputs by a power of two per
+ *              right-hand side (from the bound |X(w)| <= Nt max|x|, found by
+ *              one extra pass over the input), both scales applied in the FP32
+ *              epilogue.  The same bytes and tensor work as BF16X2. */
+typedef enum {
+  FFTMV_GEMV_NATIVE = 0,
+  FFTMV_GEMV_F64X2F32 = 1,
+  FFTMV_GEMV_BF16X2 = 2,
+  FFTMV_GEMV_F16X2 = 3
+} fftmv_gemv_mode;
 
 /* Per-phase precisions, in the execution order of the operation they are set
  * for (for F*: pad and FFT act on d, IFFT and unpad on the output m). */

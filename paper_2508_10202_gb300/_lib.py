@@ -15,7 +15,7 @@ FFTMV_OK = 0
 STATUS = {0: "FFTMV_OK", -1: "FFTMV_EINVAL", -2: "FFTMV_ENOMEM", -3: "FFTMV_EUNSUPPORTED",
           -4: "FFTMV_ECUDA", -5: "FFTMV_ESTATE"}
 FFTMV_F64, FFTMV_F32 = 0, 1
-FFTMV_GEMV_NATIVE, FFTMV_GEMV_F64X2F32, FFTMV_GEMV_BF16X2 = 0, 1, 2
+FFTMV_GEMV_NATIVE, FFTMV_GEMV_F64X2F32, FFTMV_GEMV_BF16X2, FFTMV_GEMV_F16X2 = 0, 1, 2, 3
 FFTMV_FORWARD, FFTMV_ADJOINT = 0, 1
 FFTMV_IO_F64, FFTMV_IO_F32 = 0, 1
 

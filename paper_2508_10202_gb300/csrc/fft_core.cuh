@@ -31,6 +31,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <type_traits>
 
@@ -772,7 +773,9 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
     constexpr int G = NCH < 8 ? NCH : 8;
     constexpr int NG = NCH / G;
     using Vec = typename std::conditional<G == 8, uint4, typename std::conditional<G == 4, uint2, uint32_t>::type>::type;
-    __nv_bfloat16* B = static_cast<__nv_bfloat16*>(d.X);
+    unsigned short* B = static_cast<unsigned short*>(d.X);
+    const bool f16 = d.tc_inv_scale != nullptr;
+    const float isc = f16 ? d.tc_inv_scale[b] : 1.f;
     const int ch = b / d.tc_KC, q = b - ch * d.tc_KC;
     const int64_t jr = (int64_t)ch * d.tc_N + q, ji = jr + d.tc_KC;
     const int64_t row_el = (int64_t)d.out_cols * Nf;   // bf16 per B row
@@ -802,7 +805,7 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
           zc[u] = buf[swz<C>(wc * NP + cg / 2 + u)];
         }
       }
-      __align__(16) __nv_bfloat16 h[4][G];   // rows: Re hi, Re lo, Im hi, Im lo
+      __align__(16) unsigned short h[4][G];   // rows: Re hi, Re lo, Im hi, Im lo (bf16 or FP16 bits)
 #pragma unroll
       for (int u = 0; u < G; ++u) {
         float fr = 0.f, fi = 0.f;
@@ -816,13 +819,22 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
             xr = A::half(A::add(A::re(z), A::re(y)));
             xi = A::half(A::sub(A::im(z), A::im(y)));
           }
-          fr = A::to_f(xr);
-          fi = A::to_f(xi);
+          fr = A::to_f(xr) * isc;
+          fi = A::to_f(xi) * isc;
         }
-        h[0][u] = __float2bfloat16(fr);
-        h[1][u] = __float2bfloat16(fr - __bfloat162float(h[0][u]));
-        h[2][u] = __float2bfloat16(fi);
-        h[3][u] = __float2bfloat16(fi - __bfloat162float(h[2][u]));
+        if (f16) {   // x = hi + lo in FP16 after the power-of-two scale
+          const __half rh = __float2half_rn(fr), ih = __float2half_rn(fi);
+          h[0][u] = __half_as_ushort(rh);
+          h[1][u] = __half_as_ushort(__float2half_rn(fr - __half2float(rh)));
+          h[2][u] = __half_as_ushort(ih);
+          h[3][u] = __half_as_ushort(__float2half_rn(fi - __half2float(ih)));
+        } else {
+          const __nv_bfloat16 rh = __float2bfloat16(fr), ih = __float2bfloat16(fi);
+          h[0][u] = __bfloat16_as_ushort(rh);
+          h[1][u] = __bfloat16_as_ushort(__float2bfloat16(fr - __bfloat162float(rh)));
+          h[2][u] = __bfloat16_as_ushort(ih);
+          h[3][u] = __bfloat16_as_ushort(__float2bfloat16(fi - __bfloat162float(ih)));
+        }
       }
       const int sh = d.tc_group_log2;
       const int64_t off = (((int64_t)(c >> sh) * Nf + w) << sh) + (c & ((1 << sh) - 1));

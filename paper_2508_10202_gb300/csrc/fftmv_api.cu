@@ -123,6 +123,8 @@ struct fftmv_op {
   float4* fhat_df = nullptr;  // FP32 hi/lo pairs
   float2* fhat32 = nullptr;   // FP32
   void* fhat_bf16 = nullptr;  // bf16 planes [Nf][Re hi, Re lo, Im hi, Im lo][Nd][ldn] (tensor cores)
+  void* fhat_f16 = nullptr;   // FP16 planes of F-hat_w / fscale16[w], same layout
+  float* fscale16 = nullptr;  // [Nf] powers of two
   fftmv_precision prec[2]{};
   cudaMemPool_t pool = nullptr;
   unsigned int* status = nullptr;  // device status word written by bounded waits
@@ -159,19 +161,21 @@ int check_prec(const fftmv_precision* p) {
   const int32_t v[5] = {p->pad, p->fft, p->gemv, p->ifft, p->unpad};
   for (int i = 0; i < 5; ++i)
     if (v[i] != FFTMV_F64 && v[i] != FFTMV_F32) return fail(FFTMV_EINVAL, "phase %d precision %d is not F64/F32", i, v[i]);
-  if (p->gemv_mode != FFTMV_GEMV_NATIVE && p->gemv_mode != FFTMV_GEMV_F64X2F32 && p->gemv_mode != FFTMV_GEMV_BF16X2)
+  if (p->gemv_mode != FFTMV_GEMV_NATIVE && p->gemv_mode != FFTMV_GEMV_F64X2F32 && p->gemv_mode != FFTMV_GEMV_BF16X2 &&
+      p->gemv_mode != FFTMV_GEMV_F16X2)
     return fail(FFTMV_EINVAL, "gemv_mode %d unknown", p->gemv_mode);
   if (p->gemv_mode == FFTMV_GEMV_F64X2F32 && p->gemv != FFTMV_F64)
     return fail(FFTMV_EINVAL, "gemv_mode F64X2F32 needs an FP64 GEMV phase");
-  if (p->gemv_mode == FFTMV_GEMV_BF16X2 && p->gemv != FFTMV_F32)
-    return fail(FFTMV_EINVAL, "gemv_mode BF16X2 accumulates in FP32: it needs an FP32 GEMV phase");
+  if ((p->gemv_mode == FFTMV_GEMV_BF16X2 || p->gemv_mode == FFTMV_GEMV_F16X2) && p->gemv != FFTMV_F32)
+    return fail(FFTMV_EINVAL, "gemv_mode %s accumulates in FP32: it needs an FP32 GEMV phase",
+                p->gemv_mode == FFTMV_GEMV_BF16X2 ? "BF16X2" : "F16X2");
   if (p->fft_mode != FFTMV_GEMV_NATIVE && p->fft_mode != FFTMV_GEMV_F64X2F32)
     return fail(FFTMV_EINVAL, "fft_mode %d unknown", p->fft_mode);
   return FFTMV_OK;
 }
 
 int gemv_kind(const fftmv_precision& p) {
-  if (p.gemv_mode == FFTMV_GEMV_BF16X2) return GEMV_TC;
+  if (p.gemv_mode == FFTMV_GEMV_BF16X2 || p.gemv_mode == FFTMV_GEMV_F16X2) return GEMV_TC;
   if (p.gemv == FFTMV_F32) return GEMV_F32;
   return p.gemv_mode == FFTMV_GEMV_F64X2F32 ? GEMV_DF : GEMV_F64;
 }
@@ -195,6 +199,8 @@ void release(fftmv_op* op) {
   cudaFree(op->fhat_df);
   cudaFree(op->fhat32);
   cudaFree(op->fhat_bf16);
+  cudaFree(op->fhat_f16);
+  cudaFree(op->fscale16);
   cudaFree(op->status);
   if (op->pool) cudaMemPoolDestroy(op->pool);
   for (auto& s : op->free_sets)
@@ -226,6 +232,7 @@ CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
   if (c.kind == GEMV_TC) {  // B operand planes (TcDesc), 2 J ldb Nf bf16
     c.in_ld = tc_ldb((int)c.Cin);
     c.in_hat = align256(tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld));
+    if (p.gemv_mode == FFTMV_GEMV_F16X2) c.in_hat += align256((size_t)K * 12);   // per-RHS max, scale, 1/scale
   } else {
     c.in_hat = align256((size_t)K * op->Nf * c.in_ld * fmt_bytes(c.in_fmt));
   }
@@ -265,15 +272,24 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     f.pair_ok = (reinterpret_cast<uintptr_t>(x) % (2 * esz) == 0) && f.x_ld_t % 2 == 0 && f.x_ld_b % 2 == 0;
   }
   cudaError_t e = cudaSuccess;
+  const bool f16 = c.kind == GEMV_TC && p.gemv_mode == FFTMV_GEMV_F16X2;
+  float* b_scale = nullptr;
   if (c.kind == GEMV_TC) {
     const TcShape t = tc_shape((int)K);
     f.tc_KC = t.KC;
     f.tc_N = t.N;
     f.tc_J = t.J;
     f.tc_group_log2 = fwd ? 3 : 6;
+    const size_t bbytes = tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld);
     // B rows no right-hand side fills (chunk padding, a short last chunk) must read as zero
-    if (2 * t.KC < t.N || (int)K % t.KC != 0)
-      e = cudaMemsetAsync(in_hat, 0, tc_operand_bytes((int)K, (int)op->Nf, (int)c.in_ld), s);
+    if (2 * t.KC < t.N || (int)K % t.KC != 0) e = cudaMemsetAsync(in_hat, 0, bbytes, s);
+    if (f16 && e == cudaSuccess) {   // per-RHS powers of two for the FP16 spectra
+      unsigned int* absmax = reinterpret_cast<unsigned int*>(static_cast<char*>(in_hat) + align256(bbytes));
+      b_scale = reinterpret_cast<float*>(absmax + K);
+      float* inv = b_scale + K;
+      e = launch_rhs_scales(x, io == FFTMV_IO_F32, (int)K, op->Nt * c.Cin, (int)op->Nt, absmax, b_scale, inv, s);
+      f.tc_inv_scale = inv;
+    }
   }
   if (e == cudaSuccess) e = launch_rfft_fwd(f, io == FFTMV_IO_F32, fprec, s);
   if (ev) cudaEventRecord(ev[1], s);
@@ -291,7 +307,9 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     g.status = op->status;
     if (c.kind == GEMV_TC) {
       TcDesc t{};
-      t.A = op->fhat_bf16;
+      t.A = f16 ? op->fhat_f16 : op->fhat_bf16;
+      t.a_scale = f16 ? op->fscale16 : nullptr;
+      t.b_scale = b_scale;
       t.B = in_hat;
       t.y = out_hat;
       t.Nf = (int)op->Nf;
@@ -601,9 +619,14 @@ int fftmv_set_precision(fftmv_op* op, int which, const fftmv_precision* prec) {
     CUDA_TRY(cudaMalloc(&op->fhat32, n * sizeof(float2)));
     CUDA_TRY(launch_convert_fhat(kind, op->fhat64, op->fhat32, n, 0));
     CUDA_TRY(cudaStreamSynchronize(0));
-  } else if (kind == GEMV_TC && !op->fhat_bf16) {
+  } else if (kind == GEMV_TC && prec->gemv_mode == FFTMV_GEMV_BF16X2 && !op->fhat_bf16) {
     CUDA_TRY(cudaMalloc(&op->fhat_bf16, n * 4 * 2));
     CUDA_TRY(launch_convert_bf16x2(op->fhat64, op->fhat_bf16, (int)op->Nf, (int)op->Nd, (int)op->ldn, 0));
+    CUDA_TRY(cudaStreamSynchronize(0));
+  } else if (kind == GEMV_TC && prec->gemv_mode == FFTMV_GEMV_F16X2 && !op->fhat_f16) {
+    CUDA_TRY(cudaMalloc(&op->fhat_f16, n * 4 * 2));
+    CUDA_TRY(cudaMalloc(&op->fscale16, op->Nf * sizeof(float)));
+    CUDA_TRY(launch_convert_f16x2(op->fhat64, op->fhat_f16, op->fscale16, (int)op->Nf, (int)op->Nd, (int)op->ldn, 0));
     CUDA_TRY(cudaStreamSynchronize(0));
   }
   op->prec[which] = *prec;
@@ -687,7 +710,7 @@ int fftmv_get_info(const fftmv_op* op, fftmv_info* out) {
   out->device = op->device;
   const size_t n = (size_t)op->Nf * op->Nd * op->ldn;
   out->fhat_bytes = n * sizeof(double2) + (op->fhat_df ? n * sizeof(float4) : 0) + (op->fhat32 ? n * sizeof(float2) : 0) +
-                    (op->fhat_bf16 ? n * 8 : 0);
+                    (op->fhat_bf16 ? n * 8 : 0) + (op->fhat_f16 ? n * 8 : 0);
   return FFTMV_OK;
 }
 

@@ -65,6 +65,7 @@ struct FwdDesc {
   int pad_single;          // round the loaded input to FP32 (pad phase in FP32)
   int tc_KC, tc_N, tc_J;   // FMT_TC: right-hand sides per chunk, rows per chunk, rows per plane
   int tc_group_log2;       // FMT_TC: log2 of the channels per contiguous run of a B row, 3 (F) or 6 (F*)
+  const float* tc_inv_scale;  // FMT_TC: null for bf16 hi/lo; else FP16 hi/lo of X * tc_inv_scale[b]
   int pair_ok;             // x and its strides allow loading channels (2q, 2q+1) as one vector
 };
 
@@ -119,11 +120,19 @@ struct TcDesc {
   int adjoint;             // 0: F (contract over n), 1: F* (contract over r, A read transposed)
   int64_t y_ld_b;
   unsigned int* status;
+  const float* a_scale;    // null: bf16 planes; else FP16 planes of F-hat_w / a_scale[w] ...
+  const float* b_scale;    // ... and of the spectra / b_scale[b]: results times a_scale[w] b_scale[b]
 };
 cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s);
 size_t tc_operand_bytes(int K, int Nf, int ldb);   // B planes
 int tc_ldb(int n);                                   // n rounded up to the 64-wide K block
 cudaError_t launch_convert_bf16x2(const double2* master, void* out, int Nf, int Nd, int ldn, cudaStream_t s);
+// master FP64 F-hat -> FP16 planes of F-hat_w / scale[w], scale[w] a power of two per frequency
+cudaError_t launch_convert_f16x2(const double2* master, void* out, float* scale, int Nf, int Nd, int ldn, cudaStream_t s);
+// per right-hand side b of x (K blocks of n values, double or float): scale[b] = 2^(ceil log2(Nt max|x_b|) - 14)
+// and inv[b] = 1/scale[b] (1 for an all-zero input); absmax: K words of scratch
+cudaError_t launch_rhs_scales(const void* x, bool x_f32, int K, int64_t n, int Nt, unsigned int* absmax, float* scale,
+                              float* inv, cudaStream_t s);
 size_t tc_smem_bytes(int N);
 
 cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, int prec, cudaStream_t s);

@@ -34,6 +34,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "fftmv_internal.h"
 #include "pipe.cuh"
@@ -109,13 +110,14 @@ __device__ __forceinline__ uint64_t umma_desc_mn_sw128(const void* smem) {
   return d;
 }
 
-// instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = n
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int n) {
-  return (1u << 4)                         // D format: F32
-         | (1u << 7)                       // A format: BF16
-         | (1u << 10)                      // B format: BF16
-         | ((uint32_t)(n >> 3) << 17)      // N / 8
-         | ((uint32_t)(TC_M >> 4) << 24);  // M / 16
+// instruction descriptor, kind::f16: A and B both BF16 (format 1) or both FP16
+// (format 0), K-major; FP32 D; M = 128, N = n
+__host__ __device__ constexpr uint32_t umma_idesc(int n, bool f16) {
+  return (1u << 4)                          // D format: F32
+         | ((f16 ? 0u : 1u) << 7)           // A format
+         | ((f16 ? 0u : 1u) << 10)          // B format
+         | ((uint32_t)(n >> 3) << 17)       // N / 8
+         | ((uint32_t)(TC_M >> 4) << 24);   // M / 16
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -161,6 +163,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 struct TcArgs {
   int Nf, M, K, KC, N, nkb;  // M: output rows (Nd for F, Nm for F*)
+  const float* a_scale;      // FP16 operands: per-frequency and per-RHS scales (null: bf16)
+  const float* b_scale;
   int J;                     // B rows per plane
   int nch, nmt;              // right-hand-side chunks and 128-row M tiles per frequency
   int64_t y_ld_b, y_ld_w;    // complex elements between right-hand sides / frequencies of y
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = umma_idesc_bf16(N) | (H ? (1u << 15) : 0u);   // bit 15: A is MN-major
+      const uint32_t idesc = umma_idesc(N, a.a_scale != nullptr) | (H ? (1u << 15) : 0u);   // bit 15: A is MN-major
       uint32_t it = 0, G = 0;   // k-blocks consumed, groups started
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         for (int kb = 0; kb < a.nkb; ++kb, ++it) {
@@ -357,14 +361,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) mbar_arrive(&drained[set]);
       }
       if (ok && row < a.M) {
+        const float sw = a.a_scale ? a.a_scale[w] : 1.f;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int q = qlo + c * 16 + i;
             const int b = ch * KC + q;
-            if (c * 16 + i < qn && b < a.K)
-              a.y[b * a.y_ld_b + (int64_t)w * a.y_ld_w + row] = make_float2(sre[c * 16 + i], sim[c * 16 + i]);
+            if (c * 16 + i < qn && b < a.K) {
+              const float sc = a.a_scale ? sw * a.b_scale[b] : 1.f;   // powers of two: exact
+              a.y[b * a.y_ld_b + (int64_t)w * a.y_ld_w + row] = make_float2(sre[c * 16 + i] * sc, sim[c * 16 + i] * sc);
+            }
           }
         }
       }
@@ -393,6 +400,90 @@ __global__ void convert_bf16x2_kernel(const double2* __restrict__ in, __nv_bfloa
     o[2 * plane] = ih;
     o[3 * plane] = __double2bfloat16(v.y - (double)__bfloat162float(ih));
   }
+}
+
+// power of two s with max / s in (2^13, 2^14]: FP16 keeps 4x headroom below its
+// largest finite value, and lo parts stay normal for entries down to 2^-17 max
+__device__ __forceinline__ double pow2_scale(double mx) {
+  if (!(mx > 0.0)) return 1.0;
+  int e;
+  const double m = frexp(mx, &e);       // mx = m 2^e, m in [0.5, 1)
+  return ldexp(1.0, (m == 0.5 ? e - 1 : e) - 14);
+}
+
+// per frequency: scale[w] from max |Re|, |Im| of F-hat_w (one CTA per frequency)
+__global__ void __launch_bounds__(1024) fhat_scale_kernel(const double2* __restrict__ in, float* __restrict__ scale,
+                                                          int64_t plane) {
+  __shared__ double red[32];
+  const double2* p = in + blockIdx.x * plane;
+  double mx = 0.0;
+  for (int64_t i = threadIdx.x; i < plane; i += blockDim.x) {
+    const double2 v = p[i];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) scale[blockIdx.x] = (float)pow2_scale(mx);
+  }
+}
+
+// master FP64 F-hat -> four FP16 planes [Nf][4][Nd][ldn] of F-hat_w / scale[w]
+__global__ void convert_f16x2_kernel(const double2* __restrict__ in, const float* __restrict__ scale,
+                                     __half* __restrict__ out, int Nd, int ldn, int64_t n) {
+  const int64_t plane = (int64_t)Nd * ldn;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = i / plane, rem = i - w * plane;
+    const double inv = 1.0 / (double)scale[w];
+    const double2 v = in[i];
+    const double re = v.x * inv, im = v.y * inv;
+    __half* o = out + w * 4 * plane + rem;
+    const __half rh = __double2half(re), ih = __double2half(im);
+    o[0] = rh;
+    o[plane] = __double2half(re - (double)__half2float(rh));
+    o[2 * plane] = ih;
+    o[3 * plane] = __double2half(im - (double)__half2float(ih));
+  }
+}
+
+// per right-hand side: max |x| over its n values (float bits order like the
+// values); a block reduction, then one atomic per CTA
+template <typename T>
+__global__ void __launch_bounds__(512) rhs_absmax_kernel(const T* __restrict__ x, int64_t n,
+                                                         unsigned int* __restrict__ absmax) {
+  __shared__ float red[16];
+  const T* p = x + (int64_t)blockIdx.y * n;
+  float m0 = 0.f, m1 = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {   // two loads in flight
+    m0 = fmaxf(m0, fabsf((float)__ldcs(p + i)));
+    m1 = fmaxf(m1, fabsf((float)__ldcs(p + i + stride)));
+  }
+  if (i < n) m0 = fmaxf(m0, fabsf((float)__ldcs(p + i)));
+  float mx = fmaxf(m0, m1);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) atomicMax(absmax + blockIdx.y, __float_as_uint(mx));
+  }
+}
+
+// scale[b] = power of two bounding Nt max|x_b| as above (|X(w)| <= sum_t |x_t| <= Nt max|x|)
+__global__ void rhs_scale_kernel(const unsigned int* __restrict__ absmax, int K, int Nt, float* __restrict__ scale,
+                                 float* __restrict__ inv) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= K) return;
+  // the float max may round down by half an ulp: 2^-23 of headroom more than covers it
+  const double sc = pow2_scale((double)__uint_as_float(absmax[b]) * (double)Nt * (1.0 + 0x1p-20));
+  scale[b] = (float)sc;
+  inv[b] = (float)(1.0 / sc);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -472,6 +563,38 @@ size_t tc_smem_bytes(int N) {
   return 1024 + TC_STAGES * stage + (2 * TC_STAGES + 4) * sizeof(uint64_t) + 16;
 }
 
+cudaError_t launch_convert_f16x2(const double2* master, void* out, float* scale, int Nf, int Nd, int ldn,
+                                 cudaStream_t s) {
+  const int64_t plane = (int64_t)Nd * ldn, n = (int64_t)Nf * plane;
+  if (n == 0) return cudaSuccess;
+  fhat_scale_kernel<<<Nf, 1024, 0, s>>>(master, scale, plane);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  const int64_t want = (n + threads - 1) / threads;
+  const int blocks = (int)(want < 152 * 32 ? want : 152 * 32);
+  convert_f16x2_kernel<<<blocks, threads, 0, s>>>(master, scale, static_cast<__half*>(out), Nd, ldn, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_scales(const void* x, bool x_f32, int K, int64_t n, int Nt, unsigned int* absmax, float* scale,
+                              float* inv, cudaStream_t s) {
+  if (K == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(absmax, 0, (size_t)K * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  // about four CTAs of 512 threads per SM over all right-hand sides, at least 32 values a thread
+  int64_t bx = (4 * 152 + K - 1) / K;
+  const int64_t most = (n + 512 * 32 - 1) / (512 * 32);
+  bx = bx > most ? most : bx;
+  bx = bx < 1 ? 1 : bx;
+  dim3 grid((unsigned)bx, K);
+  if (x_f32) rhs_absmax_kernel<float><<<grid, 512, 0, s>>>(static_cast<const float*>(x), n, absmax);
+  else rhs_absmax_kernel<double><<<grid, 512, 0, s>>>(static_cast<const double*>(x), n, absmax);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  rhs_scale_kernel<<<(K + 127) / 128, 128, 0, s>>>(absmax, K, Nt, scale, inv);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert_bf16x2(const double2* master, void* out, int Nf, int Nd, int ldn, cudaStream_t s) {
   const int64_t n = (int64_t)Nf * Nd * ldn;
   if (n == 0) return cudaSuccess;
@@ -508,6 +631,8 @@ cudaError_t launch_tc_gemm(const TcDesc& d, cudaStream_t s) {
   a.y_ld_w = H ? d.ldn : d.Nd;
   a.y = static_cast<float2*>(d.y);
   a.status = d.status;
+  a.a_scale = d.a_scale;
+  a.b_scale = d.b_scale;
   const size_t smem = tc_smem_bytes(t.N);
   auto kernel = H ? tc_gemm_kernel<true> : tc_gemm_kernel<false>;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -13,7 +13,8 @@ import numpy as np
 from . import _lib as L
 
 _PHASE_LETTERS = {"d": L.FFTMV_F64, "s": L.FFTMV_F32}
-_MODES = {"native": L.FFTMV_GEMV_NATIVE, "f64x2f32": L.FFTMV_GEMV_F64X2F32, "bf16x2": L.FFTMV_GEMV_BF16X2}
+_MODES = {"native": L.FFTMV_GEMV_NATIVE, "f64x2f32": L.FFTMV_GEMV_F64X2F32, "bf16x2": L.FFTMV_GEMV_BF16X2,
+          "f16x2": L.FFTMV_GEMV_F16X2}
 _WHICH = {"F": L.FFTMV_FORWARD, "forward": L.FFTMV_FORWARD, L.FFTMV_FORWARD: L.FFTMV_FORWARD,
           "F*": L.FFTMV_ADJOINT, "adjoint": L.FFTMV_ADJOINT, L.FFTMV_ADJOINT: L.FFTMV_ADJOINT}
 

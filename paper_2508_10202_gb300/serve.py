@@ -37,7 +37,7 @@ from .operator import Operator
 __all__ = ["Request", "Server", "ServerError", "latency_stats"]
 
 BUCKETS = (1, 2, 4, 8, 16, 32, 64)
-DEFAULT_PRECISION = {"F": ("sssss", "bf16x2"), "F*": ("sssss", "bf16x2")}
+DEFAULT_PRECISION = {"F": ("sssss", "bf16x2"), "F*": ("sssss", "f16x2")}
 
 
 class ServerError(RuntimeError):
