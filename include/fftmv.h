@@ -186,6 +186,16 @@ int fftmv_get_info(const fftmv_op* op, fftmv_info* out);
 #define FFTMV_STATUS_WAIT_TIMEOUT 1u
 int fftmv_device_status(fftmv_op* op, uint32_t* flags, int clear);
 
+/* Self-check of that mechanism (no counterpart in the paper).  One warp
+ * waits on a pipeline barrier with at most `polls` polls (1 <= polls <=
+ * 2^22, the kernels' own limit).  With complete != 0 the barrier's phase is
+ * completed first and the wait succeeds; with complete == 0 nothing completes
+ * it, the wait runs out and FFTMV_STATUS_WAIT_TIMEOUT is raised in the
+ * operator's status word, as a stalled copy pipeline would raise it.  Nothing
+ * faults or hangs either way and the context stays usable.  Stream ordered;
+ * EINVAL for polls out of range. */
+int fftmv_check_bounded_wait(fftmv_op* op, uint32_t polls, int complete, void* stream);
+
 /* Per-phase CUDA-event timers (the paper's per-phase timings).  While
  * enabled, every call records events on its stream around its three kernel
  * groups: [0] pad+FFT, [1] block matvec, [2] IFFT+unpad.  fftmv_phase_times

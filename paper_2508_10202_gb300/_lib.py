@@ -18,6 +18,7 @@ FFTMV_F64, FFTMV_F32 = 0, 1
 FFTMV_GEMV_NATIVE, FFTMV_GEMV_F64X2F32, FFTMV_GEMV_BF16X2, FFTMV_GEMV_F16X2 = 0, 1, 2, 3
 FFTMV_FORWARD, FFTMV_ADJOINT = 0, 1
 FFTMV_IO_F64, FFTMV_IO_F32 = 0, 1
+FFTMV_STATUS_WAIT_TIMEOUT = 1
 
 
 class FftmvError(RuntimeError):
@@ -54,6 +55,7 @@ SIGNATURES = {
     "fftmv_apply_ws": (_INT, [_P, _INT, _P, _P, _I64, _INT, _P, ctypes.c_size_t, _P]),
     "fftmv_get_info": (_INT, [_P, ctypes.POINTER(Info)]),
     "fftmv_device_status": (_INT, [_P, ctypes.POINTER(ctypes.c_uint32), _INT]),
+    "fftmv_check_bounded_wait": (_INT, [_P, ctypes.c_uint32, _INT, _P]),
     "fftmv_set_timing": (_INT, [_P, _INT]),
     "fftmv_phase_times": (_INT, [_P, _INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "fftmv_reset_timing": (_INT, [_P]),

@@ -16,6 +16,7 @@
 
 #include "fftmv.h"
 #include "fftmv_internal.h"
+#include "pipe.cuh"
 
 using namespace fftmv;
 
@@ -723,6 +724,38 @@ int fftmv_device_status(fftmv_op* op, uint32_t* flags, int clear) {
   CUDA_TRY(cudaMemcpy(&v, op->status, sizeof v, cudaMemcpyDeviceToHost));
   if (clear) CUDA_TRY(cudaMemset(op->status, 0, sizeof v));
   *flags = v;
+  return FFTMV_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One warp waits on a pipeline barrier that expects one arrival, polling at
+// most `polls` times, the way the copy pipelines wait for their data.  With
+// `complete` that arrival happens first and the wait succeeds; otherwise
+// nothing completes the phase and the wait runs out.
+__global__ void bounded_wait_check_kernel(unsigned int* status, uint32_t polls, int complete) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (complete && threadIdx.x == 0) mbar_arrive(&bar);
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, polls);
+  if (!ok && threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fftmv_check_bounded_wait(fftmv_op* op, uint32_t polls, int complete, void* stream) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (polls < 1 || polls > kSpinLimit) return fail(FFTMV_EINVAL, "polls = %u outside [1, %u]", polls, kSpinLimit);
+  DeviceGuard dg(op->device);
+  bounded_wait_check_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(op->status, polls, complete != 0);
+  CUDA_TRY(cudaGetLastError());
   return FFTMV_OK;
 }
 

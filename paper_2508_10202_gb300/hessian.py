@@ -15,6 +15,8 @@ unit vectors each, so the tensor-core multi-RHS path serves the whole batch.
 """
 from __future__ import annotations
 
+import contextlib
+
 __all__ = ["hessian_columns", "assemble"]
 
 
@@ -35,19 +37,25 @@ def hessian_columns(op, idx, prior_var: float = 1.0, noise_var: float = 0.0, bat
         raise ValueError("batch must be >= 1")
     dtype = dtype or torch.float64
     dev = torch.device("cuda", op.device) if hasattr(op, "device") and isinstance(op.device, int) else "cuda"
-    out = torch.empty((idx.numel(), op.Nt, op.Nd), dtype=dtype, device=dev)
-    for c0 in range(0, idx.numel(), batch):
-        ids = idx[c0:c0 + batch].to(dev)
-        k = ids.numel()
-        e = torch.zeros((k, op.Nt, op.Nd), dtype=dtype, device=dev)
-        e.view(k, -1)[torch.arange(k, device=dev), ids] = 1.0
-        x = op.rmatvec(e, stream=stream)
-        if prior_var != 1.0:
-            x.mul_(prior_var)
-        y = op.matvec(x, stream=stream)
-        if noise_var != 0.0:
-            y.view(k, -1)[torch.arange(k, device=dev), ids] += noise_var
-        out[c0:c0 + k] = y
+    # every step (the torch ops building e_i and adding the noise, and the two
+    # operator calls) is ordered on one stream
+    if isinstance(stream, int):
+        stream = torch.cuda.ExternalStream(stream)
+    ctx = torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext()
+    with ctx:
+        out = torch.empty((idx.numel(), op.Nt, op.Nd), dtype=dtype, device=dev)
+        for c0 in range(0, idx.numel(), batch):
+            ids = idx[c0:c0 + batch].to(dev)
+            k = ids.numel()
+            e = torch.zeros((k, op.Nt, op.Nd), dtype=dtype, device=dev)
+            e.view(k, -1)[torch.arange(k, device=dev), ids] = 1.0
+            x = op.rmatvec(e, stream=stream)
+            if prior_var != 1.0:
+                x.mul_(prior_var)
+            y = op.matvec(x, stream=stream)
+            if noise_var != 0.0:
+                y.view(k, -1)[torch.arange(k, device=dev), ids] += noise_var
+            out[c0:c0 + k] = y
     return out
 
 

@@ -208,6 +208,13 @@ class Operator:
         L.check(L.lib().fftmv_device_status(self.handle, ctypes.byref(v), int(bool(clear))))
         return v.value
 
+    def check_bounded_wait(self, polls: int = 1000, complete: bool = False, stream=None) -> None:
+        """Run the bounded-wait self-check: a barrier wait of at most `polls`
+        polls that succeeds (complete=True) or runs out and raises the timeout
+        bit in device_status() (complete=False).  Stream ordered."""
+        L.check(L.lib().fftmv_check_bounded_wait(self.handle, int(polls), int(bool(complete)),
+                                                 _stream_handle(stream, self.device)))
+
     # -- per-phase timers -----------------------------------------------------
     def set_timing(self, enable: bool = True) -> None:
         L.check(L.lib().fftmv_set_timing(self.handle, int(bool(enable))))

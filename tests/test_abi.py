@@ -69,6 +69,8 @@ def test_null_and_dead_handles(lib):
     assert lib.fftmv_workspace_bytes(fake, 0, 1, ctypes.byref(out)) == -5
     ms = (ctypes.c_double * 3)()
     assert lib.fftmv_phase_times(None, 0, ms, None) == -1
+    assert lib.fftmv_check_bounded_wait(None, 10, 0, None) == -1
+    assert lib.fftmv_check_bounded_wait(fake, 10, 0, None) == -5
 
 
 def test_python_precision_strings():

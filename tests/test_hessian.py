@@ -56,3 +56,26 @@ def test_columns_subset_and_errors(torch_cuda):
     with pytest.raises(ValueError):
         hessian_columns(op, [Nt * Nd])
     op.free()
+
+
+def test_columns_on_a_side_stream(torch_cuda):
+    """With stream= given, building e_i, the two operator calls and the noise
+    term all run on that stream; the result read after its synchronisation
+    equals the default-stream one bit for bit."""
+    torch = torch_cuda
+    from paper_2508_10202_gb300 import Operator
+    from paper_2508_10202_gb300.hessian import hessian_columns
+    Nt, Nd, Nm = 40, 6, 300
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=4)
+    op = Operator(torch.from_numpy(Fcol).cuda())
+    for w in ("F", "F*"):
+        op.set_precision(w, "ddddd", "f64x2f32", "f64x2f32")
+    idx = list(range(0, Nt * Nd, 7))
+    ref = hessian_columns(op, idx, prior_var=0.3, noise_var=0.02, batch=5)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    for handle in (s, s.cuda_stream):
+        got = hessian_columns(op, idx, prior_var=0.3, noise_var=0.02, batch=5, stream=handle)
+        s.synchronize()
+        assert torch.equal(got, ref)
+    op.free()
