@@ -17,7 +17,9 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 NT, ND, NM = 1000, 100, 10000
 CASES = [  # (F precision, F* precision, mode, tolerance)
     ("ddddd", "ddddd", "f64x2f32", 1e-12),
-    ("ddddd", "ddddd", "native", 1e-12),
+    # the plain FP64 path is also bench.py's reference for every error it
+    # reports, so it is held to 1e-14 here (it measures 4e-16 / 7e-16)
+    ("ddddd", "ddddd", "native", 1e-14),
     ("dssdd", "ddssd", "native", 1e-5),
 ]
 
@@ -60,7 +62,7 @@ def test_fullsize_sampled_and_adjoint(full, pf, pa, mode, tol):
     got = np.array([x[j, n] for j, n in idx])
     assert oracle.rel_l2(got, ref) <= tol
     lhs, rhs = np.vdot(y, d), np.vdot(m, x)
-    assert abs(lhs - rhs) <= max(tol, 1e-12) * np.linalg.norm(y) * np.linalg.norm(d)
+    assert abs(lhs - rhs) <= max(tol, 1e-13) * np.linalg.norm(y) * np.linalg.norm(d)
     assert np.all(np.isfinite(y)) and np.all(np.isfinite(x))
     assert op.device_status() == 0
 
