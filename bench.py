@@ -362,6 +362,61 @@ def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: in
             "algorithmic_bytes_per_call": int((Nt + 1) * Nd * Nm * 8 + K * Nt * Nm * 4 + K * Nt * Nd * 4)}
 
 
+def bench_small(torch, dev, calls: int = 2000) -> dict:
+    """The plain FP64 workload Nt=64, Nd=8, Nm=32 (F-hat 266 KB, resident in L2):
+    latency-bound, so it reports microseconds per call, issued directly and as
+    a replayed CUDA graph of caller-scratch calls; a roofline fraction means
+    nothing at this size."""
+    import synth
+    from paper_2508_10202_gb300 import Operator
+    Nt, Nd, Nm = 64, 8, 32
+    op = Operator(torch.from_numpy(synth.block_column(Nt, Nd, Nm, seed=0)).to(dev))
+    m = torch.from_numpy(synth.vectors(synth.TAG_M, Nt, Nm, seed=0)[0]).to(dev)
+    d = torch.from_numpy(synth.vectors(synth.TAG_D, Nt, Nd, seed=0)[0]).to(dev)
+    y = torch.empty((Nt, Nd), dtype=torch.float64, device=dev)
+    x = torch.empty((Nt, Nm), dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn) -> float:
+        for _ in range(20):
+            fn()
+        torch.cuda.synchronize(dev)
+        ev[0].record(s)
+        for _ in range(calls // 2):
+            fn()
+        ev[1].record(s)
+        torch.cuda.synchronize(dev)
+        return ev[0].elapsed_time(ev[1]) * 1e3 / calls      # us per matvec
+
+    def direct():
+        op.matvec(m, out=y, stream=s)
+        op.rmatvec(d, out=x, stream=s)
+    us_direct = timed(direct)
+    wf, wa = op.workspace_bytes("F", 1), op.workspace_bytes("F*", 1)
+    ws = torch.empty(max(wf, wa) + 256, dtype=torch.uint8, device=dev)
+    off = (-ws.data_ptr()) % 256
+    wsf = ws[off:off + wf]
+    wsa = ws[off:off + wa]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        op.apply_ws("F", m, y, wsf, stream=s)
+        op.apply_ws("F*", d, x, wsa, stream=s)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.graph(g, stream=s):
+        op.apply_ws("F", m, y, wsf, stream=s)
+        op.apply_ws("F*", d, x, wsa, stream=s)
+
+    def graphed():
+        with torch.cuda.stream(s):
+            g.replay()
+    us_graph = timed(graphed)
+    op.free()
+    return {"workload": "plain FP64, Nt=64 Nd=8 Nm=32, F and F* alternating", "precision": "ddddd/native",
+            "us_per_matvec_direct": us_direct, "us_per_matvec_graph": us_graph,
+            "matvec_s_graph": 1e6 / us_graph, "roofline": "not meaningful: launch- and latency-bound"}
+
+
 def bench_hessian(torch, op, Fcol, stream, batch: int = 64, batches: int = 4) -> dict:
     """Data-space Hessian columns H_d e_i = F(F* e_i) + noise (Remark 1), batch unit
     vectors per F*/F pair on the tensor cores; the full matrix needs Nd*Nt columns."""
@@ -629,6 +684,10 @@ def main(args) -> None:
     if rank == 0 and not args.no_multi:
         hess = bench_hessian(torch, op, Fcol, stream)
 
+    small = None
+    if rank == 0 and not args.no_variants:
+        small = bench_small(torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(Fcol, m, d)
@@ -654,7 +713,7 @@ def main(args) -> None:
                         "how": "relative L2 over the whole outputs against the plain FP64 path (native FP64 FMA) "
                                "on the same inputs; that path's parity with the oracle is tests/test_fullsize.py"},
             "roofline": roofline, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "variants": variants,
-            "multi_rhs": multi, "hessian": hess, "pareto": pareto, "served": served,
+            "multi_rhs": multi, "hessian": hess, "small": small, "pareto": pareto, "served": served,
             "served_p50_ms": served["load_0.9"]["p50_ms"] if served else None,
             "served_p99_ms": served["load_0.9"]["p99_ms"] if served else None,
             "setup_s": t_setup, "gen_s": t_gen,

@@ -972,16 +972,59 @@ cudaError_t inv_launch_np(const InvDesc& d, cudaStream_t s) {
 // the lengths with kernels of their own: L = 2 Nt for Nt = 64, 128, 256, 500, 1000
 #define FFTMV_FIXED_LENGTHS(X) X(128) X(256) X(512) X(1000) X(2000)
 
+// SMs of the current device, looked up once per device
+inline int fft_sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 152;
+    }
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+// Channel pairs per CTA for a grid of `groups(np)` CTAs: the shared-memory
+// tile's share (fft_pairs).  In native FP64 it is halved while the grid would
+// cover fewer SMs than the GPU has: the FP64 arithmetic of a whole CTA shares
+// one SM's FP64 pipe (about 2 DFMA per clock), so spreading the pairs over
+// more SMs shortens a small transform.  FP32 and double-float CTAs are bound
+// by their threads' dependency chains, which do not shorten with fewer pairs,
+// and keep the compile-time kernels.
+template <typename P, class Groups>
+int fft_pairs_for_grid(int L, Groups groups) {
+  int np = fft_pairs<P>(L);
+  if constexpr (std::is_same<P, double>::value) {
+    const int64_t sms = fft_sm_count();
+    while (np > 1 && groups(np) < sms) np /= 2;
+  }
+  return np;
+}
+
 template <typename Tin, typename P>
 cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
-  switch (d.plan.L) {
+  // the tensor-core B planes are written 8 channels (4 pairs) at a time
+  const int np = d.fmt == FMT_TC ? fft_pairs<P>(d.plan.L)
+                                 : fft_pairs_for_grid<P>(d.plan.L, [&](int n) {
+                                     return (int64_t)d.rows * ((d.out_cols + 2 * n - 1) / (2 * n)) * d.K;
+                                   });
+  if (np == fft_pairs<P>(d.plan.L)) {
+    switch (d.plan.L) {
 #define FFTMV_CASE(LL) \
   case LL: return fwd_launch_np<Tin, P, fft_pairs<P>(LL), LL>(d, s);
-    FFTMV_FIXED_LENGTHS(FFTMV_CASE)
+      FFTMV_FIXED_LENGTHS(FFTMV_CASE)
 #undef FFTMV_CASE
-    default: break;
+      default: break;
+    }
   }
-  switch (fft_pairs<P>(d.plan.L)) {
+  switch (np) {
     case 8: return fwd_launch_np<Tin, P, 8, 0>(d, s);
     case 4: return fwd_launch_np<Tin, P, 4, 0>(d, s);
     case 2: return fwd_launch_np<Tin, P, 2, 0>(d, s);
@@ -991,14 +1034,17 @@ cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
 
 template <typename P, typename Tout>
 cudaError_t inv_launch(const InvDesc& d, cudaStream_t s) {
-  switch (d.plan.L) {
+  const int np = fft_pairs_for_grid<P>(d.plan.L, [&](int n) { return (int64_t)((d.cols + 2 * n - 1) / (2 * n)) * d.K; });
+  if (np == fft_pairs<P>(d.plan.L)) {
+    switch (d.plan.L) {
 #define FFTMV_CASE(LL) \
   case LL: return inv_launch_np<P, Tout, fft_pairs<P>(LL), LL>(d, s);
-    FFTMV_FIXED_LENGTHS(FFTMV_CASE)
+      FFTMV_FIXED_LENGTHS(FFTMV_CASE)
 #undef FFTMV_CASE
-    default: break;
+      default: break;
+    }
   }
-  switch (fft_pairs<P>(d.plan.L)) {
+  switch (np) {
     case 8: return inv_launch_np<P, Tout, 8, 0>(d, s);
     case 4: return inv_launch_np<P, Tout, 4, 0>(d, s);
     case 2: return inv_launch_np<P, Tout, 2, 0>(d, s);

@@ -15,8 +15,8 @@ such requests for several operators kept resident on one GPU:
   different operators run concurrently on separate CUDA streams;
 * one launch per batch: each (operator, direction, size bucket) is captured
   once as a CUDA graph over static buffers (scratch supplied to the library,
-  so the graph holds kernel nodes only) and replayed; batches that do not fit
-  a graph run the direct call;
+  so the graph holds kernel and memset nodes, no allocation) and replayed;
+  batches that do not fit a graph run the direct call;
 * results are independent of the mix: every right-hand side is computed by
   the same per-column arithmetic whatever else is in its batch, and the tests
   check that a request gives the same numbers alone and in the mix.
