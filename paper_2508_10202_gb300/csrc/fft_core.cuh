@@ -235,8 +235,9 @@ template <typename P, bool INV> struct Dft<P, 5, INV> {
     const C a1 = Cx<P>::add(v[1], v[4]), b1 = Cx<P>::sub(v[1], v[4]);
     const C a2 = Cx<P>::add(v[2], v[3]), b2 = Cx<P>::sub(v[2], v[3]);
     const C x0 = v[0];
-    const C r1 = Cx<P>::add(x0, Cx<P>::add(Cx<P>::mulk(a1, KC1), Cx<P>::mulk(a2, KC2)));
-    const C r2 = Cx<P>::add(x0, Cx<P>::add(Cx<P>::mulk(a1, KC2), Cx<P>::mulk(a2, KC1)));
+    // (x0 + a1 c1) + a2 c2: two fused multiply-adds per real part in FP32 and FP64
+    const C r1 = Cx<P>::add(Cx<P>::add(x0, Cx<P>::mulk(a1, KC1)), Cx<P>::mulk(a2, KC2));
+    const C r2 = Cx<P>::add(Cx<P>::add(x0, Cx<P>::mulk(a1, KC2)), Cx<P>::mulk(a2, KC1));
     const C j1 = Cx<P>::template mmi<INV>(Cx<P>::add(Cx<P>::mulk(b1, KS1), Cx<P>::mulk(b2, KS2)));
     const C j2 = Cx<P>::template mmi<INV>(Cx<P>::sub(Cx<P>::mulk(b1, KS2), Cx<P>::mulk(b2, KS1)));
     v[0] = Cx<P>::add(x0, Cx<P>::add(a1, a2));
@@ -775,7 +776,8 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
     using Vec = typename std::conditional<G == 8, uint4, typename std::conditional<G == 4, uint2, uint32_t>::type>::type;
     unsigned short* B = static_cast<unsigned short*>(d.X);
     const bool f16 = d.tc_inv_scale != nullptr;
-    const float isc = f16 ? d.tc_inv_scale[b] : 1.f;
+    // the split's 1/2 and the FP16 path's power-of-two scale in one factor
+    const float hsc = 0.5f * (f16 ? d.tc_inv_scale[b] : 1.f);
     const int ch = b / d.tc_KC, q = b - ch * d.tc_KC;
     const int64_t jr = (int64_t)ch * d.tc_N + q, ji = jr + d.tc_KC;
     const int64_t row_el = (int64_t)d.out_cols * Nf;   // bf16 per B row
@@ -813,14 +815,14 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
           const C z = zw[u >> 1], y = zc[u >> 1];
           R xr, xi;
           if (u & 1) {
-            xr = A::half(A::add(A::im(z), A::im(y)));
-            xi = A::half(A::sub(A::re(y), A::re(z)));
+            xr = A::add(A::im(z), A::im(y));
+            xi = A::sub(A::re(y), A::re(z));
           } else {
-            xr = A::half(A::add(A::re(z), A::re(y)));
-            xi = A::half(A::sub(A::im(z), A::im(y)));
+            xr = A::add(A::re(z), A::re(y));
+            xi = A::sub(A::im(z), A::im(y));
           }
-          fr = A::to_f(xr) * isc;
-          fi = A::to_f(xi) * isc;
+          fr = A::to_f(xr) * hsc;
+          fi = A::to_f(xi) * hsc;
         }
         if (f16) {   // x = hi + lo in FP16 after the power-of-two scale
           const __half rh = __float2half_rn(fr), ih = __float2half_rn(fi);
