@@ -18,9 +18,6 @@ cudaError_t launch_irfft_inv_f64_float(const InvDesc& d, cudaStream_t s);
 cudaError_t launch_irfft_inv_f32_float(const InvDesc& d, cudaStream_t s);
 cudaError_t launch_irfft_inv_df_float(const InvDesc& d, cudaStream_t s);
 
-// shared memory of one CTA's signals: one interleaved buffer, passes in place
-size_t fft_smem_bytes(int L, int prec) { return (size_t)L * (prec == FFT_F32 ? sizeof(float2) : 16); }
-
 // one signal per CTA: at most 1024 threads x the per-thread element count
 // (16 FP32 complexes, 8 FP64 or double-float ones)
 int fft_max_length(int prec) { return prec == FFT_F32 ? 16384 : 8192; }

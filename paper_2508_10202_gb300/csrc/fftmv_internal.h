@@ -142,7 +142,6 @@ cudaError_t launch_gemv_h(int kind, const GemvDesc& d, cudaStream_t s);
 // master FP64 F-hat (double2, n elements) -> kind's storage (DF float4 or F32 float2)
 cudaError_t launch_convert_fhat(int kind, const double2* master, void* out, size_t n, cudaStream_t s);
 
-size_t fft_smem_bytes(int L, int prec);
 int fft_max_length(int prec);
 // the input / output format each GEMV kind expects / produces
 int gemv_in_fmt(int kind);
