@@ -351,6 +351,7 @@ def test_shard_simulation_on_one_gpu(torch_cuda, pr, pc):
 # --- large K in chunks within the scratch bound ------------------------------
 
 @pytest.mark.parametrize("prec,mode,fft_mode,tol", [("sssss", "bf16x2", "native", 1e-6),
+                                                    ("sssss", "f16x2", "native", 1e-6),
                                                     ("ddddd", "f64x2f32", "f64x2f32", 1e-13)])
 def test_scratch_limit_chunks_rhs(torch_cuda, prec, mode, fft_mode, tol):
     torch = torch_cuda
@@ -395,3 +396,59 @@ def test_maximum_length(torch_cuda, prec, mode, fft_mode):
     # one block more needs a longer transform than one CTA holds: refused at creation
     with pytest.raises(FftmvError, match="exceeds"):
         Operator(torch.zeros((Nt + 1, 1, 1), dtype=torch.float64, device="cuda"))
+
+
+# --- caller-supplied scratch and CUDA graphs ----------------------------------
+
+@pytest.mark.parametrize("prec,mode,fft_mode", [("ddddd", "native", "native"), ("ddddd", "f64x2f32", "f64x2f32"),
+                                                ("sssss", "native", "native"), ("sssss", "bf16x2", "native"),
+                                                ("sssss", "f16x2", "native")])
+def test_apply_ws_and_graph_replay(torch_cuda, prec, mode, fft_mode):
+    """fftmv_apply_ws with caller scratch gives the pooled call's result bit for
+    bit; captured once in a CUDA graph and replayed after new inputs are copied
+    into its static buffers, it gives the pooled result on the new inputs."""
+    torch = torch_cuda
+    from paper_2508_10202_gb300 import FftmvError
+    Nt, Nd, Nm, K = 50, 6, 90, 5
+    Fcol, m, d = make_case(Nt, Nd, Nm, K=K, seed=41)
+    op = gpu_op(torch, Fcol)
+    for w in ("F", "F*"):
+        op.set_precision(w, prec, mode, fft_mode)
+    dt = torch.float64 if prec == "ddddd" else torch.float32
+    s = torch.cuda.Stream()
+    xs = {"F": torch.from_numpy(m).to("cuda", dt), "F*": torch.from_numpy(d).to("cuda", dt)}
+    outs = {"F": torch.empty((K, Nt, Nd), dtype=dt, device="cuda"),
+            "F*": torch.empty((K, Nt, Nm), dtype=dt, device="cuda")}
+    wss = {}
+    for w in ("F", "F*"):
+        nb = op.workspace_bytes(w, K)
+        buf = torch.empty(nb + 512, dtype=torch.uint8, device="cuda")
+        off = (-buf.data_ptr()) % 256
+        wss[w] = buf[off:off + nb]
+        ref = (op.matvec if w == "F" else op.rmatvec)(xs[w])
+        op.apply_ws(w, xs[w], outs[w], wss[w], stream=s)
+        s.synchronize()
+        assert torch.equal(outs[w], ref), w
+        with pytest.raises(FftmvError):
+            op.apply_ws(w, xs[w], outs[w], wss[w][:nb - 256], stream=s)      # too small
+        with pytest.raises(FftmvError):
+            op.apply_ws(w, xs[w], outs[w], buf[off + 16:off + 16 + nb], stream=s)   # misaligned
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        op.apply_ws("F", xs["F"], outs["F"], wss["F"], stream=s)
+        op.apply_ws("F*", xs["F*"], outs["F*"], wss["F*"], stream=s)
+    m2 = synth.vectors(synth.TAG_M, Nt, Nm, k=K, seed=42)
+    d2 = synth.vectors(synth.TAG_D, Nt, Nd, k=K, seed=42)
+    with torch.cuda.stream(s):
+        xs["F"].copy_(torch.from_numpy(m2).to("cuda", dt))
+        xs["F*"].copy_(torch.from_numpy(d2).to("cuda", dt))
+        g.replay()
+    s.synchronize()
+    assert torch.equal(outs["F"], op.matvec(xs["F"]))
+    assert torch.equal(outs["F*"], op.rmatvec(xs["F*"]))
+    tol = TOL64 if prec == "ddddd" else TOL32
+    assert oracle.rel_l2(outs["F"].double().cpu().numpy(), oracle.matvec_direct(Fcol, m2.astype(
+        np.float64 if prec == "ddddd" else np.float32).astype(np.float64))) <= tol
+    assert op.device_status() == 0
+    op.free()
