@@ -8,7 +8,10 @@
 // Precision: F-hat and the spectra are each split into bfloat16 hi + lo parts
 // (x = hi + lo + O(2^-18 |x|)); the three products hi*hi + hi*lo + lo*hi
 // accumulate in FP32 in tensor memory (the lo*lo term is below 2^-16 of the
-// result).
+// result).  The FP16 mode splits the same way into FP16 (11-bit) parts after
+// exact power-of-two scaling: F-hat_w by s_w (per frequency), the spectra of
+// right-hand side b by s_b; both operands of one MMA are then FP16, and the
+// epilogue multiplies each output by s_w * s_b.
 //
 // Complex arithmetic without duplicating data: A is four planes
 // (Re hi, Re lo, Im hi, Im lo) of F-hat_w, B is [Re X | Im X] (2*KC columns,
@@ -19,8 +22,12 @@
 //
 // Tiles: one frequency, one chunk of KC <= 64 right-hand sides and 128 output
 // rows; MMA tile M = 128 (rows past the end are zero-filled by TMA, never read
-// from HBM), N = 2*KC rounded up to 16, K-step 64 bf16 (one 128-byte swizzled
-// row).  Persistent CTAs, one per SM, loop over the tiles.
+// from HBM), N = 2*KC rounded up to 16, K-step 64 16-bit values.  A is read in
+// 128-byte swizzled rows (K-major for F, MN-major for F*).  B comes as the FFT
+// wrote it: for F in 8-channel runs adjacent over frequency (16-byte rows,
+// loaded without swizzle and described as K-major core matrices), for F* in
+// 64-value rows under the 128-byte swizzle.  Persistent CTAs, one per SM, loop
+// over the tiles.
 // Warp roles: warp 0 issues TMA loads, warp 1 owns tensor memory and issues
 // the MMAs, warps 2-9 drain the accumulators (tcgen05.ld) and write the output.
 //
