@@ -3,7 +3,8 @@
 //
 // For every frequency w the operator block F-hat_w is Nd x Nm complex with
 // Nd << Nm, stored row-major with a padded row length ldn (a multiple of 8).
-// Both directions stream F-hat exactly once with 16-byte vector loads:
+// Both directions stream F-hat exactly once per pass of right-hand sides: N
+// through a bulk-copy pipeline into shared memory, H with 16-byte vector loads:
 //
 //  N (F):  d-hat_w[r] = sum_n F_w[r, n] m-hat_w[n].  A CTA owns R rows of one
 //          frequency and sweeps the whole row length; each thread keeps R
