@@ -889,7 +889,14 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   // Z_w = X_a(w) + i X_b(w) over the full circle, X(L-w) = conj X(w); the DC and
   // Nyquist terms of a real signal's spectrum are taken as real.  Thread i
   // reads channel pair i % NP at frequency i / NP (two adjacent entries).
-  constexpr int U = 4;   // loads in flight per thread
+#ifndef FFTMV_INV_LOADS25
+#define FFTMV_INV_LOADS25 16
+#endif
+  // loads in flight per thread: 16-byte complexes 4; FP32 ones 8 (4 with one
+  // pair per CTA); 16 in the 25-element kernels, whose register budget has
+  // room and whose Nf NP loads then issue in one round (L = 2000: F* at K = 64
+  // 2.76 ms against 3.06 with 4)
+  constexpr int U = sizeof(C) == 8 ? (E == 25 ? FFTMV_INV_LOADS25 : NP >= 2 ? 8 : 4) : 4;
   const C zero = A::mk(A::zero(), A::zero());
   for (int i0 = threadIdx.x; i0 < Nf * NP; i0 += U * T) {
     C a[U], bb[U];
