@@ -625,6 +625,13 @@ template <typename P>
 __host__ __device__ constexpr int fft_bound_blocks(int NP, int LC) {
   return LC > 0 && fft_elems<P>(LC) == 25 ? (fft_bound_threads<P>(NP, LC) <= 320 ? 2 : 1) : 1;
 }
+// loads in flight per thread for the inverse's spectrum assembly of a
+// compile-time length: items / threads rounded up, capped by the register budget
+__host__ __device__ constexpr int fft_inv_loads(int csize, int e, int nf, int np, int threads) {
+  const int want = (nf * np + threads - 1) / threads;
+  const int cap = csize == 8 ? (e == 25 ? 16 : 8) : 8;
+  return want < cap ? want : cap;
+}
 __host__ __device__ constexpr unsigned cmagic(int ns) {
   return ns > 1 ? (unsigned)((((unsigned long long)1 << 32) + (unsigned long long)ns - 1) / (unsigned long long)ns) : 0u;
 }
@@ -877,6 +884,7 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   using A = Ar<P>;
   using C = typename A::C;
   constexpr int E = LC > 0 ? fft_elems<P>(LC) : kFftE<P>;
+  constexpr int T_LC = LC > 0 ? fft_nthreads<P>(NP, LC, E) : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int L = LC > 0 ? LC : d.plan.L;
@@ -889,14 +897,13 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   // Z_w = X_a(w) + i X_b(w) over the full circle, X(L-w) = conj X(w); the DC and
   // Nyquist terms of a real signal's spectrum are taken as real.  Thread i
   // reads channel pair i % NP at frequency i / NP (two adjacent entries).
-#ifndef FFTMV_INV_LOADS25
-#define FFTMV_INV_LOADS25 16
-#endif
-  // loads in flight per thread: 16-byte complexes 4; FP32 ones 8 (4 with one
-  // pair per CTA); 16 in the 25-element kernels, whose register budget has
-  // room and whose Nf NP loads then issue in one round (L = 2000: F* at K = 64
-  // 2.76 ms against 3.06 with 4)
-  constexpr int U = sizeof(C) == 8 ? (E == 25 ? FFTMV_INV_LOADS25 : NP >= 2 ? 8 : 4) : 4;
+  // Loads in flight per thread.  The compile-time kernels take enough for all
+  // Nf NP of them to issue in one round, up to what their registers hold (16
+  // FP32 complexes in the 25-element kernels, 8 otherwise): at L = 2000 the
+  // FP32 F* at K = 64 takes 2.76 ms against 3.06 with 4.  The runtime-length
+  // kernels take 8 FP32 complexes (4 with one pair per CTA) or 4 wider ones.
+  constexpr int U = LC > 0 ? fft_inv_loads(sizeof(C), E, LC / 2 + 1, NP, T_LC)
+                           : (sizeof(C) == 8 && NP >= 2 ? 8 : 4);
   const C zero = A::mk(A::zero(), A::zero());
   for (int i0 = threadIdx.x; i0 < Nf * NP; i0 += U * T) {
     C a[U], bb[U];
