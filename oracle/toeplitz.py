@@ -27,6 +27,9 @@ Functions, each a plain restatement of one passage:
   definition, one at a time, for full-size spot checks.
 * :func:`relative_error_bound` - the first-order bound of Eq. (error),
   Section 3.2.1, with all algorithm constants set to one.
+* :func:`hessian_entries` - entries of the data-space Hessian
+  F G_prior F* + G_noise of Remark 1 (isotropic G_prior and G_noise), each
+  from the definition as an inner product of two block rows of F.
 
 Pins (tests/test_oracle.py) tie these to closed forms, brute force, the
 adjoint identity, causality and the spectrum facts; nothing here is compared
