@@ -25,8 +25,9 @@ Functions, each a plain restatement of one passage:
   phase computed in FP32 or FP64 as a precision string names (Section 3.2).
 * :func:`matvec_entries`, :func:`rmatvec_entries` - selected outputs of the
   definition, one at a time, for full-size spot checks.
-* :func:`relative_error_bound` - the first-order bound of Eq. (error),
-  Section 3.2.1, with all algorithm constants set to one.
+* :func:`relative_error_bound`, :func:`error_bound` - the first-order bound
+  of Eq. (error), Section 3.2.1, with all algorithm constants set to one;
+  the second picks n_m and p_c (F) or n_d and p_r (F*) from the grid.
 * :func:`hessian_entries` - entries of the data-space Hessian
   F G_prior F* + G_noise of Remark 1 (isotropic G_prior and G_noise), each
   from the definition as an inner product of two block rows of F.
@@ -44,7 +45,7 @@ __all__ = [
     "matvec_direct", "rmatvec_direct", "dense_matrix",
     "spectrum", "matvec_fft", "rmatvec_fft", "matvec_fft_spec", "rmatvec_fft_spec",
     "matvec_mixed", "rmatvec_mixed", "parse_precision",
-    "matvec_entries", "rmatvec_entries", "relative_error_bound", "rel_l2",
+    "matvec_entries", "rmatvec_entries", "relative_error_bound", "error_bound", "rel_l2",
     "hessian_entries",
 ]
 
@@ -334,6 +335,23 @@ def relative_error_bound(prec: str, Nt: int, n_inner: int, kappa: float, p: int 
     if p > 1:
         bound += e[4] * np.log2(p)
     return float(kappa * bound + c5 * e[4])
+
+
+def error_bound(prec: str, which: str, Nt: int, Nd: int, Nm: int, kappa: float, pr: int = 1, pc: int = 1) -> float:
+    """Eq. (error) for one direction on a p_r x p_c process grid (Section 3.2.1).
+
+    For F the block matvec's inner length is n_m = ceil(Nm / p_c) and the
+    reduction of phase 5 runs over the p_c processes of a grid row; for F*
+    the paper swaps in n_d = ceil(Nd / p_r) and p_r.  ``which`` is "F" or
+    "F*".  Everything else is :func:`relative_error_bound`.
+    """
+    if which == "F":
+        n, p = -(-Nm // pc), pc
+    elif which == "F*":
+        n, p = -(-Nd // pr), pr
+    else:
+        raise ValueError(f"which must be 'F' or 'F*', got {which!r}")
+    return relative_error_bound(prec, Nt, n, kappa, p)
 
 
 # ---------------------------------------------------------------------------

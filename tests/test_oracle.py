@@ -291,6 +291,103 @@ def test_mixed_single_phases_have_fp32_error_level(prec):
     assert ea <= 10 * oracle.relative_error_bound(prec, Nt, Nd, kappa)
 
 
+# --- Eq. (error), Section 3.2.1: values worked by hand -------------------------
+#
+# The bound is kappa [c1 e1 + (cF ed + c2 e2 + c4 e4) log2(Nt) + c3 e3 n + c5 e5 log2(p)]
+# with every c_i = 1, c1 = 0 for an FP64 pad, n = n_m = ceil(Nm / p_c) and p = p_c
+# for F, n = n_d = ceil(Nd / p_r) and p = p_r for F*, plus e5 outside kappa when
+# the unpad phase is FP32 (reading R10).  e_i is the unit roundoff of phase i:
+# us = 2^-24 (FP32), ud = 2^-53 (FP64).  The case below has Nt = 1024
+# (log2 Nt = 10 exactly), Nd = 100, Nm = 5000, kappa = 4.  Each expected value
+# is written as (a, b) for a ud + b us:
+#   ddddd F : 4 [(ud+ud+ud) 10 + ud 5000]            = 4 * 5030 ud        -> (20120, 0)
+#   ddddd F*: 4 [30 ud + 100 ud]                      = 4 * 130 ud         -> (520, 0)
+#   dssdd F : 4 [(ud+us+ud) 10 + us 5000]             = 4 (20 ud + 5010 us) -> (80, 20040)
+#   dssdd F*: 4 [(ud+us+ud) 10 + us 100]              = 4 (20 ud + 110 us)  -> (80, 440)
+#   ddsdd F : 4 [30 ud + us 5000]                     -> (120, 20000)
+#   ddsdd F*: 4 [30 ud + us 100]                      -> (120, 400)
+#   ddssd F*: 4 [(ud+ud+us) 10 + us 100]              = 4 (20 ud + 110 us)  -> (80, 440)
+#   sdddd F : 4 [us + 30 ud + 5000 ud]                -> (20120, 4)
+#   dddds F : 4 [30 ud + 5000 ud] + us                -> (20120, 1)
+# On a 2 x 4 grid (p_r = 2, p_c = 4): n_m = 1250, log2 p_c = 2; n_d = 50, log2 p_r = 1:
+#   ddddd F : 4 [30 ud + 1250 ud + 2 ud]              = 4 * 1282 ud        -> (5128, 0)
+#   ddddd F*: 4 [30 ud + 50 ud + 1 ud]                = 4 * 81 ud          -> (324, 0)
+#   dddds F : 4 [30 ud + 1250 ud + 2 us] + us         -> (5120, 9)
+#   dssdd F*: 4 [(ud+us+ud) 10 + 50 us + 1 ud]        = 4 (21 ud + 60 us)  -> (84, 240)
+BOUND_CASES = [
+    # prec, which, p_r, p_c, (a, b)
+    ("ddddd", "F", 1, 1, (20120, 0)),
+    ("ddddd", "F*", 1, 1, (520, 0)),
+    ("dssdd", "F", 1, 1, (80, 20040)),
+    ("dssdd", "F*", 1, 1, (80, 440)),
+    ("ddsdd", "F", 1, 1, (120, 20000)),
+    ("ddsdd", "F*", 1, 1, (120, 400)),
+    ("ddssd", "F*", 1, 1, (80, 440)),
+    ("sdddd", "F", 1, 1, (20120, 4)),
+    ("dddds", "F", 1, 1, (20120, 1)),
+    ("ddddd", "F", 2, 4, (5128, 0)),
+    ("ddddd", "F*", 2, 4, (324, 0)),
+    ("dddds", "F", 2, 4, (5120, 9)),
+    ("dssdd", "F*", 2, 4, (84, 240)),
+]
+US, UD = 2.0 ** -24, 2.0 ** -53
+
+
+def _bound_pin_failures(fn):
+    """The hand-worked cases that ``fn`` (signature of oracle.error_bound) misses."""
+    bad = []
+    for prec, which, pr, pc, (a, b) in BOUND_CASES:
+        want = a * UD + b * US
+        got = fn(prec, which, 1024, 100, 5000, 4.0, pr=pr, pc=pc)
+        if not abs(got - want) <= 1e-15 * want:
+            bad.append((prec, which, pr, pc, got, want))
+    return bad
+
+
+def test_error_bound_hand_values():
+    assert _bound_pin_failures(oracle.error_bound) == []
+
+
+def test_relative_error_bound_hand_values():
+    # the same cases through the lower-level entry point, n and p given directly
+    for prec, which, pr, pc, (a, b) in BOUND_CASES:
+        n, p = (-(-5000 // pc), pc) if which == "F" else (-(-100 // pr), pr)
+        got = oracle.relative_error_bound(prec, 1024, n, 4.0, p)
+        assert abs(got - (a * UD + b * US)) <= 1e-15 * (a * UD + b * US), (prec, which, pr, pc)
+
+
+def test_error_bound_rejects_planted_mistakes():
+    # plausible slips in restating Eq. (error); each must fail a hand-worked case
+    def base(prec, Nt, n, kappa, p, c1_d=0.0, lg=True, unpad=True, pterm=True):
+        eps = {"s": US, "d": UD}
+        e = [eps[c] for c in prec]
+        c1 = c1_d if prec[0] == "d" else 1.0
+        b = c1 * e[0] + (UD + e[1] + e[3]) * (np.log2(Nt) if lg else 1.0) + e[2] * n
+        if pterm and p > 1:
+            b += e[4] * np.log2(p)
+        return kappa * b + ((0.0 if prec[4] == "d" else 1.0) * e[4] if unpad else 0.0)
+
+    def with_grid(inner, swap=False, ceil=True):
+        def fn(prec, which, Nt, Nd, Nm, kappa, pr=1, pc=1):
+            fwd = (which == "F") != swap
+            num, q = (Nm, pc) if fwd else (Nd, pr)
+            n = -(-num // q) if ceil else num
+            return inner(prec, Nt, n, kappa, pc if which == "F" else pr)
+        return fn
+
+    assert _bound_pin_failures(with_grid(base)) == []          # the restatement itself passes
+    mutants = {
+        "n_d and n_m swapped": with_grid(base, swap=True),
+        "grid ignored in n": with_grid(base, ceil=False),
+        "log2 Nt dropped": with_grid(lambda *a: base(*a, lg=False)),
+        "c1 e1 charged for an FP64 pad": with_grid(lambda *a: base(*a, c1_d=1.0)),
+        "FP32 unpad term omitted": with_grid(lambda *a: base(*a, unpad=False)),
+        "reduction term dropped": with_grid(lambda *a: base(*a, pterm=False)),
+    }
+    for name, fn in mutants.items():
+        assert _bound_pin_failures(fn), name
+
+
 def test_parse_precision():
     assert oracle.parse_precision("dssdd")[1] == np.float32
     with pytest.raises(ValueError):
