@@ -618,8 +618,8 @@ def main(args) -> None:
     ab = algorithmic_bytes(Nt, Nd, Nm, fhat_entry_bytes(*HEADLINE))
     gemv_ms = (tf[1] + ta[1]) / (nf + na)
     achieved = ab / (gemv_ms * 1e-3) / 1e9
-    # DRAM bytes per launch of the same two kernels from ncu --set full at Nm=1000,
-    # scaled x10 to the full operator (profiles/gemv_df_Nm1000_full.md)
+    # DRAM bytes per launch of the same two kernels from ncu --set full at Nm=2000,
+    # scaled x5 to the full operator (profiles/gemv_df_paper_shape_Nm2000_full.md)
     traffic = GEMV_DF_TRAFFIC if (Nt, Nd, Nm) == (NT, ND, NM) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "gemv_n_kernel<KindDF> (F) / gemv_h_kernel<KindDF> (F*)",

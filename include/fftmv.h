@@ -122,8 +122,11 @@ typedef struct {
  * transformed once, always in FP64, Section 3.2).
  *   F_col  : Nt*Nd*Nm doubles, [k][r][n] row-major, host or device memory;
  *            read during the call only.
- *   Nt, Nd, Nm >= 1.  Nt is limited by the shared-memory FFT (L <= 7264;
- *            EUNSUPPORTED beyond).
+ *   Nt, Nd, Nm >= 1.  Nt is limited by the shared-memory FFT: L <= 8192
+ *            (Nt <= 4096) for the FP64 and double-float FFTs, which the
+ *            setup FFT always uses; EUNSUPPORTED beyond.  (The FP32 FFT
+ *            itself reaches L = 16384, but an operator is only created where
+ *            its FP64 setup FFT runs.)
  *   stream : cudaStream_t used for the setup work (NULL = legacy default).
  *   out    : receives the new handle.
  * Creates on the current CUDA device.  Synchronous: returns after F-hat is
@@ -197,8 +200,10 @@ int fftmv_device_status(fftmv_op* op, uint32_t* flags, int clear);
 int fftmv_check_bounded_wait(fftmv_op* op, uint32_t polls, int complete, void* stream);
 
 /* Per-phase CUDA-event timers (the paper's per-phase timings).  While
- * enabled, every call records events on its stream around its three kernel
- * groups: [0] pad+FFT, [1] block matvec, [2] IFFT+unpad.  fftmv_phase_times
+ * enabled, every fftmv_matvec / fftmv_rmatvec call records events on its
+ * stream around its three kernel groups: [0] pad+FFT, [1] block matvec,
+ * [2] IFFT+unpad.  fftmv_apply_ws and fftmv_apply_noalloc calls are not
+ * timed (they create no event objects).  fftmv_phase_times
  * waits for the recorded events and returns the summed milliseconds and the
  * number of calls for F or F*; reset clears them. */
 int fftmv_set_timing(fftmv_op* op, int enable);
@@ -225,12 +230,17 @@ int fftmv_reset_timing(fftmv_op* op);
  * Scratch.  The spectra live in one file-scope device array inside the
  * library.  Every GPU that loads the library holds that array until the
  * process exits.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls on a device share the array, and
- * it keeps the previous call's contents: the kernels overwrite every scratch
- * entry before they read it, so nothing is cleared in between.  Calls that
- * overlap on the GPU (different streams, or different operators on the same
- * device) race on the array; serialise them.
+ * address (cudaGetSymbolAddress) with that device current, and so does the
+ * first call after a device reset (the address is cached per context); make
+ * that first call before any stream capture: while the stream is capturing,
+ * the lookup is refused with FFTMV_ESTATE.  All calls on a device share the
+ * array, and it keeps the previous call's contents: the kernels overwrite
+ * every scratch entry they read, or the call clears it first, so no call
+ * depends on what an earlier one left.  Calls that overlap on the GPU
+ * (different streams, or different operators on the same device) race on
+ * the array; serialise them.
+ * Timing.  These calls record no per-phase events (that would need event
+ * objects): fftmv_phase_times leaves them out.
  * Errors as for fftmv_matvec.  Stream ordered and asynchronous. */
 int fftmv_apply_noalloc(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io_dtype,
                         void* stream);

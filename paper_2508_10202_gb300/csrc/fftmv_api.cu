@@ -826,23 +826,62 @@ namespace {
 
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-char* g_noalloc_addr[kNoallocMaxDevices] = {};
+struct NoallocSlot {
+  void* ctx = nullptr;   // the context the address belongs to
+  char* addr = nullptr;
+};
+NoallocSlot g_noalloc[kNoallocMaxDevices];
+
+// The current context (driver API, reached through the runtime's entry-point
+// query so that the library links against the runtime only).
+using CtxGetCurrentFn = int (*)(void**);
+void* current_context() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 // Device address of the scratch array on `device` (which must be current).
 // In host code the array's name is only a host-side stand-in, so the address
-// is looked up once per device and cached.
-int noalloc_address(int device, char** out) {
+// is looked up per device and cached together with the context it belongs
+// to: after a device reset the primary context, and with it the array's
+// address, is new, and the lookup runs again.  The lookup may load the
+// library's module, which must not happen inside a stream capture, so it is
+// refused while `s` is capturing.
+int noalloc_address(int device, cudaStream_t s, char** out) {
   if (device < 0 || device >= kNoallocMaxDevices)
     return fail(FFTMV_EUNSUPPORTED, "device %d beyond the %d devices the no-alloc path tracks", device,
                 kNoallocMaxDevices);
+  void* ctx = current_context();
   std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_addr[device]) {
+  NoallocSlot& slot = g_noalloc[device];
+  if (!slot.addr || !ctx || slot.ctx != ctx) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      cs = cudaStreamCaptureStatusNone;
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(FFTMV_ESTATE,
+                  "fftmv_apply_noalloc: the first call on a device (or after a device reset) looks up the scratch "
+                  "array's address; make it once before capturing the stream");
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, fftmv_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(fftmv_noalloc_scratch)");
-    g_noalloc_addr[device] = static_cast<char*>(p);
+    slot.addr = static_cast<char*>(p);
+    slot.ctx = ctx;
   }
-  *out = g_noalloc_addr[device];
+  *out = slot.addr;
   return FFTMV_OK;
 }
 
@@ -874,11 +913,11 @@ extern "C" int fftmv_apply_noalloc(fftmv_op* op, int which, const void* in, void
   }
   if (!is_device_ptr(in) || !is_device_ptr(out))
     return fail(FFTMV_EINVAL, "fftmv_apply_noalloc takes device pointers only (host I/O would need staging memory)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* ws = nullptr;
-  if ((rc = noalloc_address(op->device, &ws))) return rc;
+  if ((rc = noalloc_address(op->device, s, &ws))) return rc;
   char* in_hat = ws;
   char* out_hat = ws + c.in_hat;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = launch_phases(op, which, c, in, out, in_hat, out_hat, K, io, s, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "no-alloc matvec kernels");
   return FFTMV_OK;

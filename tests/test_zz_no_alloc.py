@@ -7,8 +7,10 @@ allocation failing or a pool growing mid-run.  Its intermediate spectra live
 in a fixed 64 MiB device array inside the library instead of the operator's
 pool.  This test calls it through the C ABI twice in a row (the array keeps
 the previous call's contents) and compares each result with the pooled entry
-point's, within the FP64 tolerance of the other parity tests.  It lives in
-its own file, named to be collected last.
+point's, within the tolerance of the other parity tests (FP64: 1e-12;
+configurations with an FP32 phase: 1e-5), for the double-float and native
+FP64 modes, the two tensor-core modes and FP32 I/O.  It lives in its own file,
+named to be collected last.
 """
 import ctypes
 
@@ -63,6 +65,67 @@ def test_noalloc_matches_pooled_entry_points(env, mode):
         assert oracle.rel_l2(x.cpu().numpy(), ref_m) <= TOL64, call
     # and against the oracle itself
     assert oracle.rel_l2(y.cpu().numpy(), oracle.matvec_direct(Fcol, m.cpu().numpy())) <= TOL64
+    op.free()
+
+
+TOL32 = 1e-5   # configurations with an FP32 phase (tests/test_tensor.py)
+
+
+@pytest.mark.parametrize("mode", ["bf16x2", "f16x2"])
+@pytest.mark.parametrize("K", [3, 65])
+@pytest.mark.parametrize("io", ["f64", "f32"])
+def test_noalloc_tensor_core_modes(env, mode, K, io):
+    # The tensor-core modes put more in the fixed array: the bf16/FP16 B planes
+    # (cleared first when a chunk has padding rows: K = 3 pads each 6-row chunk
+    # to 16, K = 65 leaves a one-RHS last chunk) and, for FP16, the per-RHS
+    # maxima and scales behind them.  Each call must match the pooled call.
+    torch, Operator, L, lib = env
+    Nt, Nd, Nm = 64, 8, 32
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=2)
+    dt = np.float64 if io == "f64" else np.float32
+    m = torch.from_numpy(synth.vectors(synth.TAG_M, Nt, Nm, k=K, seed=2).astype(dt)).cuda()
+    d = torch.from_numpy(synth.vectors(synth.TAG_D, Nt, Nd, k=K, seed=2).astype(dt)).cuda()
+    op = Operator(torch.from_numpy(Fcol).cuda())
+    op.set_precision("F", "sssss", mode)
+    op.set_precision("F*", "sssss", mode)
+    stream = torch.cuda.current_stream()
+    ref_d = op.matvec(m).double().cpu().numpy()
+    ref_m = op.rmatvec(d).double().cpu().numpy()
+    tdt = torch.float64 if io == "f64" else torch.float32
+    for call in range(2):
+        y = torch.full((K, Nt, Nd), float("nan"), dtype=tdt, device="cuda")
+        x = torch.full((K, Nt, Nm), float("nan"), dtype=tdt, device="cuda")
+        assert _noalloc(lib, op, L.FFTMV_FORWARD, m, y, stream) == 0, lib.fftmv_last_error()
+        assert _noalloc(lib, op, L.FFTMV_ADJOINT, d, x, stream) == 0, lib.fftmv_last_error()
+        torch.cuda.synchronize()
+        assert oracle.rel_l2(y.double().cpu().numpy(), ref_d) <= TOL32, call
+        assert oracle.rel_l2(x.double().cpu().numpy(), ref_m) <= TOL32, call
+    assert oracle.rel_l2(y.double().cpu().numpy(), oracle.matvec_direct(Fcol, m.double().cpu().numpy())) <= TOL32
+    assert op.device_status() == 0
+    op.free()
+
+
+def test_noalloc_fp32_io_double_float(env):
+    # FP32 inputs and outputs through the FP64-class path
+    torch, Operator, L, lib = env
+    Nt, Nd, Nm, K = 64, 8, 32, 2
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=3)
+    m = torch.from_numpy(synth.vectors(synth.TAG_M, Nt, Nm, k=K, seed=3).astype(np.float32)).cuda()
+    d = torch.from_numpy(synth.vectors(synth.TAG_D, Nt, Nd, k=K, seed=3).astype(np.float32)).cuda()
+    op = Operator(torch.from_numpy(Fcol).cuda())
+    op.set_precision("F", "ddddd", "f64x2f32")
+    op.set_precision("F*", "ddddd", "f64x2f32")
+    stream = torch.cuda.current_stream()
+    ref_d = op.matvec(m).double().cpu().numpy()
+    ref_m = op.rmatvec(d).double().cpu().numpy()
+    for call in range(2):
+        y = torch.full((K, Nt, Nd), float("nan"), dtype=torch.float32, device="cuda")
+        x = torch.full((K, Nt, Nm), float("nan"), dtype=torch.float32, device="cuda")
+        assert _noalloc(lib, op, L.FFTMV_FORWARD, m, y, stream) == 0, lib.fftmv_last_error()
+        assert _noalloc(lib, op, L.FFTMV_ADJOINT, d, x, stream) == 0, lib.fftmv_last_error()
+        torch.cuda.synchronize()
+        assert oracle.rel_l2(y.double().cpu().numpy(), ref_d) <= TOL64, call
+        assert oracle.rel_l2(x.double().cpu().numpy(), ref_m) <= TOL64, call
     op.free()
 
 
