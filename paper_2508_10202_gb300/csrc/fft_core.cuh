@@ -665,6 +665,13 @@ template <typename P, typename Tin>
 __device__ __forceinline__ typename Ar<P>::R load_real(const void* p, int64_t i, bool pad_single) {
   return cvt_real<P, Tin>(__ldg(static_cast<const Tin*>(p) + i), pad_single);
 }
+// the same cast after an exact power-of-two scale `sc` in FP64 (range scaling:
+// the value then fits the FP32 exponent range of the double-float format)
+template <typename P, typename Tin>
+__device__ __forceinline__ typename Ar<P>::R cvt_real_scaled(Tin x, bool pad_single, double sc) {
+  const double v = pad_single ? (double)(float)x : (double)x;
+  return Ar<P>::from_d(v * sc);
+}
 
 // store one complex value (re, im) of precision P into format fmt
 template <typename P>
@@ -710,6 +717,14 @@ __device__ __forceinline__ typename Ar<P>::C load_cx(const void* X, int64_t i, i
   }
 }
 
+// an FP64 (FMT_C128) spectrum value times the power of two sc, loaded into precision P
+template <typename P>
+__device__ __forceinline__ typename Ar<P>::C load_cx_scaled(const void* X, int64_t i, double sc) {
+  using A = Ar<P>;
+  const double2 v = __ldg(static_cast<const double2*>(X) + i);
+  return A::mk(A::from_d(v.x * sc), A::from_d(v.y * sc));
+}
+
 // Forward: pad + real FFT; grid (row x channel group, K).  A CTA owns NP
 // adjacent channel pairs (2 NP channels); pair p is the complex signal
 // x_{c0+2p} + i x_{c0+2p+1}.  The first radix pass reads the samples straight
@@ -736,6 +751,9 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   const C* tw = static_cast<const C*>(d.tw);
   const C zero = A::mk(A::zero(), A::zero());
 
+  // range scaling: right-hand side b is divided by 2^e_b as it loads
+  const bool scaled = d.in_absmax != nullptr;
+  const double insc = scaled ? ldexp(1.0, -range_exp(d.in_absmax[b])) : 1.0;
   auto gsrc = [&](int t, int p, int) -> C {
     const int c = c0 + 2 * p;
     if (t >= d.Nt || c >= d.cols) return zero;
@@ -743,11 +761,14 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
     if (d.pair_ok && c + 1 < d.cols) {   // both channels in one 8- or 16-byte load
       using V = typename std::conditional<sizeof(Tin) == 4, float2, double2>::type;
       const V v = __ldg(reinterpret_cast<const V*>(static_cast<const Tin*>(d.x) + o));
+      if (scaled)
+        return A::mk(cvt_real_scaled<P, Tin>(v.x, d.pad_single, insc), cvt_real_scaled<P, Tin>(v.y, d.pad_single, insc));
       return A::mk(cvt_real<P, Tin>(v.x, d.pad_single), cvt_real<P, Tin>(v.y, d.pad_single));
     }
-    const R a = load_real<P, Tin>(d.x, o, d.pad_single);
-    const R bb = c + 1 < d.cols ? load_real<P, Tin>(d.x, o + 1, d.pad_single) : A::zero();
-    return A::mk(a, bb);
+    const Tin* xp = static_cast<const Tin*>(d.x) + o;
+    const Tin xa = __ldg(xp), xb = c + 1 < d.cols ? __ldg(xp + 1) : Tin(0);
+    if (scaled) return A::mk(cvt_real_scaled<P, Tin>(xa, d.pad_single, insc), cvt_real_scaled<P, Tin>(xb, d.pad_single, insc));
+    return A::mk(cvt_real<P, Tin>(xa, d.pad_single), cvt_real<P, Tin>(xb, d.pad_single));
   };
   auto sdst = [&](int, int, int e, C v) { buf[swz<C>(e)] = v; };
   auto ssrc = [&](int, int, int e) -> C { return buf[swz<C>(e)]; };
@@ -866,6 +887,15 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   }
 }
 
+// v (the scaled result) in FP64 times s1 s2, then the output cast
+template <typename Tout, typename P>
+__device__ __forceinline__ void store_real_scaled(void* y, int64_t i, typename Ar<P>::R v, bool unpad_single, double s1,
+                                                  double s2) {
+  const double r = Ar<P>::to_d(v) * s1 * s2;
+  if (unpad_single || sizeof(Tout) == 4) static_cast<Tout*>(y)[i] = (Tout)(float)r;
+  else static_cast<Tout*>(y)[i] = (Tout)r;
+}
+
 template <typename Tout, typename P>
 __device__ __forceinline__ void store_real(void* y, int64_t i, typename Ar<P>::R v, bool unpad_single) {
   if (unpad_single || sizeof(Tout) == 4) {
@@ -905,6 +935,8 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   constexpr int U = LC > 0 ? fft_inv_loads(sizeof(C), E, LC / 2 + 1, NP, T_LC)
                            : (sizeof(C) == 8 && NP >= 2 ? 8 : 4);
   const C zero = A::mk(A::zero(), A::zero());
+  const bool midsc = d.rhs_absmax != nullptr && d.in_fmt == FMT_C128 && d.mid_exp != 0;
+  const double midf = midsc ? ldexp(1.0, d.mid_exp) : 1.0;
   for (int i0 = threadIdx.x; i0 < Nf * NP; i0 += U * T) {
     C a[U], bb[U];
 #pragma unroll
@@ -917,6 +949,9 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
         const float4 v = __ldg(reinterpret_cast<const float4*>(static_cast<const float2*>(d.X) + Xo + w * d.X_ld_w + ca));
         a[u] = A::mk(A::from_f(v.x), A::from_f(v.y));
         bb[u] = A::mk(A::from_f(v.z), A::from_f(v.w));
+      } else if (midsc) {   // FP64 spectra brought into the double-float range
+        a[u] = in && ca < d.cols ? load_cx_scaled<P>(d.X, Xo + w * d.X_ld_w + ca, midf) : zero;
+        bb[u] = in && cb < d.cols ? load_cx_scaled<P>(d.X, Xo + w * d.X_ld_w + cb, midf) : zero;
       } else {
         a[u] = in && ca < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + ca, d.in_fmt) : zero;
         bb[u] = in && cb < d.cols ? load_cx<P>(d.X, Xo + w * d.X_ld_w + cb, d.in_fmt) : zero;
@@ -942,10 +977,24 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   if constexpr (LC > 0) cpasses<P, true, NP, E, LC, 0, cplan<P>(LC).npass - 1>(T, tw, ssrc, sdst);
   else inplace_passes<P, true, NP, E>(d.plan, 0, d.plan.npass - 1, tw, ssrc, sdst);
   const Kc inv_L{d.inv_L, d.inv_L_hi, d.inv_L_lo};
+  // range scaling: outputs of right-hand side b times 2^(e_b + out_exp), in two
+  // exact steps (each factor a normal double; the product may not be)
+  const bool scaled = d.rhs_absmax != nullptr;
+  double s1 = 1.0, s2 = 1.0;
+  if (scaled) {
+    const int e = range_exp(d.rhs_absmax[b]) + d.out_exp;
+    s1 = ldexp(1.0, e / 2);
+    s2 = ldexp(1.0, e - e / 2);
+  }
   auto gdst = [&](int t, int p, int, C v) {
     const int c = c0 + 2 * p;
     if (t >= d.Nt || c >= d.cols) return;
     const int64_t o = b * d.y_ld_b + t * d.y_ld_t + c;
+    if (scaled) {
+      store_real_scaled<Tout, P>(d.y, o, A::mulk(A::re(v), inv_L), d.unpad_single, s1, s2);
+      if (c + 1 < d.cols) store_real_scaled<Tout, P>(d.y, o + 1, A::mulk(A::im(v), inv_L), d.unpad_single, s1, s2);
+      return;
+    }
     store_real<Tout, P>(d.y, o, A::mulk(A::re(v), inv_L), d.unpad_single);
     if (c + 1 < d.cols) store_real<Tout, P>(d.y, o + 1, A::mulk(A::im(v), inv_L), d.unpad_single);
   };

@@ -135,6 +135,7 @@ struct fftmv_op {
   double acc_ms[2][3] = {};
   int64_t calls[2] = {};
   size_t scratch_limit = 0;  // 0: kCallScratchBudget
+  int fexp = 0;              // range exponent of F-hat: max |Re, Im| / 2^fexp in [1, 2)
 };
 
 namespace {
@@ -211,12 +212,28 @@ void release(fftmv_op* op) {
   cudaGetLastError();
 }
 
+// Range scaling.  The double-float format keeps FP32's exponent range, so a
+// call that runs any phase in it scales its data by exact powers of two:
+// F-hat by 2^-fexp (stored so), each right-hand side by 2^-e_b from its
+// largest magnitude (found by one pass over the input), and the outputs back
+// by 2^(e_b + fexp) in FP64 at the unpad.  Values then stay in [1, 2) at
+// their largest inside the double-float phases, whatever their magnitude in
+// FP64.  The tensor-core modes and all-native configurations are not scaled.
+bool range_scaled(const fftmv_precision& p) {
+  const int kind = gemv_kind(p);
+  if (kind == GEMV_TC) return false;
+  if (kind == GEMV_DF) return true;
+  return p.fft_mode == FFTMV_GEMV_F64X2F32 && (p.fft == FFTMV_F64 || p.ifft == FFTMV_F64);
+}
+
 // Scratch layout of one call: the two spectra and optional host-I/O staging.
 struct CallPlan {
   int kind, in_fmt, out_fmt;
   int64_t Cin, Cout;       // input / output channels
   int64_t in_ld, out_ld;   // spectral row length of the input / output side
   size_t in_hat, out_hat;  // bytes
+  bool scaled;             // range scaling: K absmax words at in_hat + absmax_off
+  size_t absmax_off;
 };
 
 CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
@@ -236,6 +253,11 @@ CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
     if (p.gemv_mode == FFTMV_GEMV_F16X2) c.in_hat += align256((size_t)K * 12);   // per-RHS max, scale, 1/scale
   } else {
     c.in_hat = align256((size_t)K * op->Nf * c.in_ld * fmt_bytes(c.in_fmt));
+  }
+  c.scaled = range_scaled(p);
+  if (c.scaled) {
+    c.absmax_off = c.in_hat;
+    c.in_hat += align256((size_t)K * sizeof(unsigned long long));
   }
   c.out_hat = align256((size_t)K * op->Nf * c.out_ld * fmt_bytes(c.out_fmt));
   return c;
@@ -273,6 +295,13 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     f.pair_ok = (reinterpret_cast<uintptr_t>(x) % (2 * esz) == 0) && f.x_ld_t % 2 == 0 && f.x_ld_b % 2 == 0;
   }
   cudaError_t e = cudaSuccess;
+  unsigned long long* absmax = nullptr;
+  if (c.scaled) {   // per-RHS largest magnitude of the input, for the range scaling
+    absmax = reinterpret_cast<unsigned long long*>(static_cast<char*>(in_hat) + c.absmax_off);
+    e = cudaMemsetAsync(absmax, 0, (size_t)K * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = launch_absmax(x, io == FFTMV_IO_F32, (int)K, op->Nt * c.Cin, absmax, s);
+    f.in_absmax = absmax;
+  }
   const bool f16 = c.kind == GEMV_TC && p.gemv_mode == FFTMV_GEMV_F16X2;
   float* b_scale = nullptr;
   if (c.kind == GEMV_TC) {
@@ -348,6 +377,11 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     v.inv_L = 1.0 / (double)op->L;
     v.inv_L_hi = (float)v.inv_L;
     v.inv_L_lo = (float)(v.inv_L - (double)v.inv_L_hi);
+    v.rhs_absmax = absmax;
+    // FP64 spectra of the native block matvec come back to the double-float
+    // range before the inverse; F-hat's exponent returns at the unpad
+    v.mid_exp = c.kind == GEMV_F64 ? -op->fexp : 0;
+    v.out_exp = (c.kind == GEMV_F64 || c.kind == GEMV_DF) ? op->fexp : 0;
     e = launch_irfft_inv(v, iprec, io == FFTMV_IO_F32, s);
   }
   if (ev) cudaEventRecord(ev[3], s);
@@ -586,7 +620,18 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
     }
     cudaFree(stage);
   }
-  if ((rc = cu(cudaStreamSynchronize(s), "setup synchronize"))) return rc;
+  {  // range exponent of F-hat (largest |Re|, |Im| over all entries)
+    unsigned long long* mx = nullptr;
+    if ((rc = cu(cudaMalloc(&mx, sizeof *mx), "cudaMalloc(setup max)"))) return rc;
+    unsigned long long bits = 0;
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof *mx, s);
+    if (e == cudaSuccess) e = launch_absmax(op->fhat64, false, 1, (int64_t)(Nf * Nd * ldn * 2), mx, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, mx, sizeof bits, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(mx);
+    if ((rc = cu(e, "setup range exponent"))) return rc;
+    op->fexp = range_exp(bits);
+  }
 
   cudaMemPoolProps props{};
   props.allocType = cudaMemAllocationTypePinned;
@@ -614,11 +659,11 @@ int fftmv_set_precision(fftmv_op* op, int which, const fftmv_precision* prec) {
   const size_t n = (size_t)op->Nf * op->Nd * op->ldn;
   if (kind == GEMV_DF && !op->fhat_df) {
     CUDA_TRY(cudaMalloc(&op->fhat_df, n * sizeof(float4)));
-    CUDA_TRY(launch_convert_fhat(kind, op->fhat64, op->fhat_df, n, 0));
+    CUDA_TRY(launch_convert_fhat(kind, op->fhat64, op->fhat_df, n, op->fexp, 0));
     CUDA_TRY(cudaStreamSynchronize(0));
   } else if (kind == GEMV_F32 && !op->fhat32) {
     CUDA_TRY(cudaMalloc(&op->fhat32, n * sizeof(float2)));
-    CUDA_TRY(launch_convert_fhat(kind, op->fhat64, op->fhat32, n, 0));
+    CUDA_TRY(launch_convert_fhat(kind, op->fhat64, op->fhat32, n, 0, 0));
     CUDA_TRY(cudaStreamSynchronize(0));
   } else if (kind == GEMV_TC && prec->gemv_mode == FFTMV_GEMV_BF16X2 && !op->fhat_bf16) {
     CUDA_TRY(cudaMalloc(&op->fhat_bf16, n * 4 * 2));

@@ -67,6 +67,10 @@ struct FwdDesc {
   int tc_group_log2;       // FMT_TC: log2 of the channels per contiguous run of a B row, 3 (F) or 6 (F*)
   const float* tc_inv_scale;  // FMT_TC: null for bf16 hi/lo; else FP16 hi/lo of X * tc_inv_scale[b]
   int pair_ok;             // x and its strides allow loading channels (2q, 2q+1) as one vector
+  // Range scaling of the FP64-class path (null: none).  in_absmax[b] holds the
+  // bits of max |x_b| as a double; the kernel divides right-hand side b by the
+  // power of two 2^e_b, e_b = range_exp(in_absmax[b]), as it loads it.
+  const unsigned long long* in_absmax;
 };
 
 // Inverse real FFT of Hermitian half spectra followed by unpad (phases 4-5 fused).
@@ -86,6 +90,12 @@ struct InvDesc {
   int pair_ok;             // FMT_C64 X and its strides allow loading channels (2q, 2q+1) as one float4
   double inv_L;            // 1/L in FP64 and as an FP32 hi/lo pair
   float inv_L_hi, inv_L_lo;
+  // Range scaling (null rhs_absmax: none): FMT_C128 spectra are multiplied by
+  // 2^mid_exp as they load, and every output of right-hand side b by
+  // 2^(range_exp(rhs_absmax[b]) + out_exp) as it is stored (in FP64, before
+  // the output cast).
+  const unsigned long long* rhs_absmax;
+  int mid_exp, out_exp;
 };
 
 // Per-frequency block matvec (phase 3) for K right-hand sides.
@@ -139,8 +149,22 @@ cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, int prec, cudaStream_
 cudaError_t launch_irfft_inv(const InvDesc& d, int prec, bool out_f32, cudaStream_t s);
 cudaError_t launch_gemv_n(int kind, const GemvDesc& d, cudaStream_t s);
 cudaError_t launch_gemv_h(int kind, const GemvDesc& d, cudaStream_t s);
-// master FP64 F-hat (double2, n elements) -> kind's storage (DF float4 or F32 float2)
-cudaError_t launch_convert_fhat(int kind, const double2* master, void* out, size_t n, cudaStream_t s);
+// master FP64 F-hat (double2, n elements) -> kind's storage (DF float4 of F-hat * 2^-fexp, or F32 float2)
+cudaError_t launch_convert_fhat(int kind, const double2* master, void* out, size_t n, int fexp, cudaStream_t s);
+
+// Range scaling of the FP64-class path.  absmax[b] (b < K) receives the bits
+// of max |x| over the n values of right-hand side b (double or float input),
+// as a double; the caller zeroes it first.
+cudaError_t launch_absmax(const void* x, bool x_f32, int K, int64_t n, unsigned long long* absmax, cudaStream_t s);
+// the exponent e with max / 2^e in [1, 2) for the bits of a non-negative
+// double max; 0 for zero, -1022 for subnormals, 1023 for inf and NaN
+__host__ __device__ inline int range_exp(unsigned long long bits) {
+  const int biased = (int)((bits >> 52) & 0x7FF);
+  if (bits == 0) return 0;
+  if (biased == 0) return -1022;
+  if (biased == 0x7FF) return 1023;
+  return biased - 1023;
+}
 
 int fft_max_length(int prec);
 // the input / output format each GEMV kind expects / produces

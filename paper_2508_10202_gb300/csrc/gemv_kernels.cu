@@ -385,10 +385,15 @@ __global__ void __launch_bounds__(T) gemv_h_kernel(GemvDesc d) {
   }
 }
 
-// master FP64 F-hat -> stored kind
-__global__ void convert_df_kernel(const double2* __restrict__ in, float4* __restrict__ out, size_t n) {
+// master FP64 F-hat -> stored kind.  The double-float form holds F-hat times
+// the power of two `mul` (exact), which brings its largest entry into [1, 2):
+// FP32 hi/lo pairs have FP32's exponent range, so this keeps every operator
+// whose entries fit FP64 representable, and the inverse FFT multiplies back.
+__global__ void convert_df_kernel(const double2* __restrict__ in, float4* __restrict__ out, size_t n, double mul) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double2 v = in[i];
+    double2 v = in[i];
+    v.x *= mul;
+    v.y *= mul;
     const float hr = (float)v.x, hi = (float)v.y;
     out[i] = make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
   }
@@ -499,12 +504,56 @@ cudaError_t launch_gemv_h(int kind, const GemvDesc& d, cudaStream_t s) {
   }
 }
 
-cudaError_t launch_convert_fhat(int kind, const double2* master, void* out, size_t n, cudaStream_t s) {
+cudaError_t launch_convert_fhat(int kind, const double2* master, void* out, size_t n, int fexp, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int threads = 256;
   const int blocks = (int)((n + threads - 1) / threads < (size_t)152 * 32 ? (n + threads - 1) / threads : 152 * 32);
-  if (kind == GEMV_DF) convert_df_kernel<<<blocks, threads, 0, s>>>(master, static_cast<float4*>(out), n);
+  if (kind == GEMV_DF) convert_df_kernel<<<blocks, threads, 0, s>>>(master, static_cast<float4*>(out), n, ldexp(1.0, -fexp));
   else convert_f32_kernel<<<blocks, threads, 0, s>>>(master, static_cast<float2*>(out), n);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// max |x| over the n values of right-hand side blockIdx.y, as the bits of a
+// non-negative double (their integer order is the order of the values); a
+// block reduction, then one atomicMax per CTA
+template <typename T>
+__global__ void __launch_bounds__(512) absmax_kernel(const T* __restrict__ x, int64_t n,
+                                                     unsigned long long* __restrict__ absmax) {
+  __shared__ double red[16];
+  const T* p = x + (int64_t)blockIdx.y * n;
+  double m0 = 0.0, m1 = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {   // two loads in flight
+    m0 = fmax(m0, fabs((double)__ldcs(p + i)));
+    m1 = fmax(m1, fabs((double)__ldcs(p + i + stride)));
+  }
+  if (i < n) m0 = fmax(m0, fabs((double)__ldcs(p + i)));
+  double mx = fmax(m0, m1);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) atomicMax(absmax + blockIdx.y, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_absmax(const void* x, bool x_f32, int K, int64_t n, unsigned long long* absmax, cudaStream_t s) {
+  if (K == 0) return cudaSuccess;
+  // about four CTAs of 512 threads per SM over all right-hand sides, at least 32 values a thread
+  int64_t bx = (4 * 152 + K - 1) / K;
+  const int64_t most = (n + 512 * 32 - 1) / (512 * 32);
+  bx = bx > most ? most : bx;
+  bx = bx < 1 ? 1 : bx;
+  dim3 grid((unsigned)bx, K);
+  if (x_f32) absmax_kernel<float><<<grid, 512, 0, s>>>(static_cast<const float*>(x), n, absmax);
+  else absmax_kernel<double><<<grid, 512, 0, s>>>(static_cast<const double*>(x), n, absmax);
   return cudaGetLastError();
 }
 

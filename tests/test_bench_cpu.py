@@ -1,0 +1,42 @@
+"""Host-side pieces of bench.py (no GPU): the CPU baseline's blocked oracle run
+and the reference arm's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_blocked_oracle_equals_direct():
+    import bench
+    Nt, Nd, Nm = 16, 7, 9
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=4, decay=200.0)
+    m = synth.vectors(synth.TAG_M, Nt, Nm, seed=4)[0]
+    d = synth.vectors(synth.TAG_D, Nt, Nd, seed=4)[0]
+    full = bench.OracleFull(Fcol, m, d, rows_per_block=3)
+    assert len(full.blocks) == 3 and full.blocks[-1] == (6, 7)
+    y, x = full.step()
+    assert oracle.rel_l2(y, oracle.matvec_direct(Fcol, m)) <= 1e-13
+    assert oracle.rel_l2(x, oracle.rmatvec_direct(Fcol, d)) <= 1e-13
+
+
+def test_reference_arm_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--Nt", "16",
+                        "--Nd", "5", "--Nm", "12", "--steps", "3", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 3 and line["warmup"] == 1
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert "whole" in line["cpu_baseline"]["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+    # the timed steps are the whole operator: value and ms_per_step agree
+    assert abs(line["value"] - 2e3 / line["ms_per_step"]) <= 1e-6 * line["value"]
+    assert np.isfinite(line["value"])

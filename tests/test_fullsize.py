@@ -73,3 +73,51 @@ def test_fullsize_host_io_matches_device_io(full):
     y_dev = op.matvec(torch.from_numpy(m).cuda()).cpu().numpy()
     y_host = op.matvec(torch.from_numpy(m).pin_memory()).numpy()
     np.testing.assert_array_equal(y_dev, y_host)
+
+
+# --- the paper's own shape, Nm = 5000, mantissas perturbed (Section 4.2.1) ----
+
+PAPER_NM = 5000
+PAPER_CASES = [  # (which, precision, gemv mode, fft mode, tolerance)
+    ("F", "dssdd", "native", "native", 1e-6),        # the paper's optimum for F
+    ("F", "dssdd", "native", "f64x2f32", 1e-6),
+    ("F*", "ddssd", "native", "f64x2f32", 1e-6),     # the paper's optimum for F* (SBGEMV and IFFT in FP32)
+    ("F", "ddddd", "f64x2f32", "f64x2f32", 1e-12),
+    ("F*", "ddddd", "f64x2f32", "f64x2f32", 1e-12),
+]
+
+
+@pytest.fixture(scope="module")
+def paper():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_2508_10202_gb300 import Operator, build
+    build.build()
+    Fcol = synth.block_column(NT, ND, PAPER_NM, seed=0, decay=200.0, perturb=True)
+    m = synth.vectors(synth.TAG_M, NT, PAPER_NM, seed=0, perturb=True)[0]
+    d = synth.vectors(synth.TAG_D, NT, ND, seed=0, perturb=True)[0]
+    op = Operator(Fcol)
+    yield torch, Fcol, m, d, op
+    op.free()
+
+
+@pytest.mark.parametrize("which,prec,mode,fft_mode,tol", PAPER_CASES)
+def test_paper_shape_sampled(paper, which, prec, mode, fft_mode, tol, record_property):
+    torch, Fcol, m, d, op = paper
+    op.set_precision(which, prec, mode, fft_mode)
+    if which == "F":
+        y = op.matvec(torch.from_numpy(m).cuda()).cpu().numpy()
+        idx = sample_idx(60, NT, ND, 3)
+        ref = oracle.matvec_entries(Fcol, m, idx)
+        got = np.array([y[i, r] for i, r in idx])
+    else:
+        y = op.rmatvec(torch.from_numpy(d).cuda()).cpu().numpy()
+        idx = sample_idx(60, NT, PAPER_NM, 4)
+        ref = oracle.rmatvec_entries(Fcol, d, idx)
+        got = np.array([y[j, n] for j, n in idx])
+    err = oracle.rel_l2(got, ref)
+    record_property("rel_l2_sampled", err)
+    assert err <= tol, err
+    assert np.all(np.isfinite(y))
+    assert op.device_status() == 0

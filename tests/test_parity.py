@@ -52,6 +52,50 @@ MODES64 = [("ddddd", "native"), ("ddddd", "f64x2f32")]
 MODE_PAIRS = [("native", "native"), ("f64x2f32", "f64x2f32"), ("native", "f64x2f32"), ("f64x2f32", "native")]
 
 
+# --- range: the FP64-class formats keep FP32's exponent range ----------------
+# Every configuration that runs a phase in the double-float format scales F-hat
+# and each right-hand side by exact powers of two, so operators and inputs
+# anywhere in the FP64 range keep FP64-class accuracy.  The all-native
+# configuration needs no scaling and is checked alongside.
+
+RANGE_SCALES = [(110, 110), (110, -110), (-110, 110), (-110, -110), (600, 400), (-600, -400), (-130, 0), (0, 140)]
+
+
+@pytest.mark.parametrize("Nt,Nd,Nm", [(64, 8, 32), (50, 7, 99)])
+@pytest.mark.parametrize("fexp,xexp", RANGE_SCALES)
+@pytest.mark.parametrize("mode,fft_mode", MODE_PAIRS)
+def test_fp64_range(torch_cuda, Nt, Nd, Nm, fexp, xexp, mode, fft_mode):
+    torch = torch_cuda
+    Fcol, m, d = make_case(Nt, Nd, Nm, seed=5)
+    Fcol = np.ldexp(Fcol, fexp)
+    m, d = np.ldexp(m[0], xexp), np.ldexp(d[0], xexp)
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", "ddddd", mode, fft_mode)
+    op.set_precision("F*", "ddddd", mode, fft_mode)
+    y, x = run_both(torch, op, m, d)
+    assert np.all(np.isfinite(y)) and np.all(np.isfinite(x))
+    assert oracle.rel_l2(y, oracle.matvec_direct(Fcol, m)) <= TOL64
+    assert oracle.rel_l2(x, oracle.rmatvec_direct(Fcol, d)) <= TOL64
+    op.free()
+
+
+@pytest.mark.parametrize("fexp,xexp", [(110, -100), (-110, 100), (-100, -20)])
+def test_fp64_class_range_fp32_io(torch_cuda, fexp, xexp):
+    # FP32 inputs and outputs (in FP32 range), an operator far outside it
+    torch = torch_cuda
+    Fcol, m, d = make_case(64, 8, 32, K=2, seed=6)
+    Fcol = np.ldexp(Fcol, fexp)
+    m32, d32 = np.ldexp(m, xexp).astype(np.float32), np.ldexp(d, xexp).astype(np.float32)
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", "ddddd", "f64x2f32", "f64x2f32")
+    op.set_precision("F*", "ddddd", "f64x2f32", "f64x2f32")
+    y, x = run_both(torch, op, m32, d32)
+    # the exact result of the FP32 inputs, rounded once to FP32 at the output
+    assert oracle.rel_l2(y, oracle.matvec_direct(Fcol, m32.astype(np.float64))) <= 2e-7
+    assert oracle.rel_l2(x, oracle.rmatvec_direct(Fcol, d32.astype(np.float64))) <= 2e-7
+    op.free()
+
+
 # --- the plain FP64 workload: Nt=64, Nd=8, Nm=32, seed 0 ---------------------
 
 @pytest.mark.parametrize("prec,mode", MODES64)
