@@ -547,7 +547,7 @@ def bench_serving(torch, dev, n_cap: int = 600, n_load: int = 2000, seed: int = 
         ops[name] = Operator(col)
         del col
     setup_s = time.perf_counter() - t0
-    srv = Server(ops, budget_bytes=SERVE_BUDGET, n_streams=4)
+    srv = Server(ops, budget_bytes=SERVE_BUDGET, n_streams=4, keep_outputs=False)
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
     pools = {}

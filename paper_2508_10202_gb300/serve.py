@@ -99,7 +99,8 @@ class _Batch:
 
 class Server:
     def __init__(self, operators: dict[str, Operator], budget_bytes: int, n_streams: int = 4,
-                 max_batch_rhs: int = 64, precision: dict | None = None, graphs: bool = True):
+                 max_batch_rhs: int = 64, precision: dict | None = None, graphs: bool = True,
+                 keep_outputs: bool = True):
         if not operators:
             raise ServerError("no operators")
         self.ops = dict(operators)
@@ -115,6 +116,9 @@ class Server:
         self.in_use = 0
         self.max_batch_rhs = int(max_batch_rhs)
         self.graphs_enabled = graphs
+        # False: a finished request drops its output (load generators that
+        # only measure latency would otherwise hold every result in HBM)
+        self.keep_outputs = keep_outputs
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
         self.free_streams = collections.deque(range(n_streams))
         self.queue: collections.deque[Request] = collections.deque()
@@ -201,6 +205,8 @@ class Server:
             now = time.perf_counter() if now is None else now
             for r in b.reqs:
                 r.status, r.t_done = "done", now
+                if not self.keep_outputs:
+                    r.out = None
                 self.completed.append(r)
             self.inflight.remove(b)
             self.in_use -= b.nbytes
