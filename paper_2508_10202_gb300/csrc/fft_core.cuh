@@ -402,6 +402,14 @@ template <typename P, int R1, int R2, bool INV, bool HALF> struct DftComp {
         const int m = (n2 * k1) % R;
         if (m == 0) {
           y[n2 * R1 + k1] = u[k1];
+        } else if constexpr (std::is_same<P, float>::value || std::is_same<P, double>::value) {
+          // u * (c -+ i s) with fused multiply-adds: c and s of the table are
+          // the cosine and sine of 2 pi m / R
+          using Rl = typename A::R;
+          const Rl re = A::re(u[k1]), im = A::im(u[k1]);
+          const Rl c = (Rl)tt.c[m].d, sn = (Rl)tt.s[m].d;
+          y[n2 * R1 + k1] = INV ? A::mk(fma(re, c, -(im * sn)), fma(im, c, re * sn))
+                                : A::mk(fma(re, c, im * sn), fma(im, c, -(re * sn)));
         } else {   // u * (c -+ i s)
           const typename A::R re = A::re(u[k1]), im = A::im(u[k1]);
           const typename A::R cr = A::mulk(re, tt.c[m]), ci = A::mulk(im, tt.c[m]);
@@ -752,8 +760,9 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   const C zero = A::mk(A::zero(), A::zero());
 
   // range scaling: right-hand side b is divided by 2^e_b as it loads
-  const bool scaled = d.in_absmax != nullptr;
-  const double insc = scaled ? ldexp(1.0, -range_exp(d.in_absmax[b])) : 1.0;
+  const int in_exp = d.in_absmax != nullptr ? range_exp(d.in_absmax[b]) : 0;
+  const bool scaled = in_exp != 0;
+  const double insc = scaled ? ldexp(1.0, -in_exp) : 1.0;
   auto gsrc = [&](int t, int p, int) -> C {
     const int c = c0 + 2 * p;
     if (t >= d.Nt || c >= d.cols) return zero;
@@ -804,8 +813,9 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
     using Vec = typename std::conditional<G == 8, uint4, typename std::conditional<G == 4, uint2, uint32_t>::type>::type;
     unsigned short* B = static_cast<unsigned short*>(d.X);
     const bool f16 = d.tc_inv_scale != nullptr;
-    // the split's 1/2 and the FP16 path's power-of-two scale in one factor
-    const float hsc = 0.5f * (f16 ? d.tc_inv_scale[b] : 1.f);
+    // the FP16 path's power-of-two scale; the split's 1/2 is applied by the
+    // contraction's epilogue (the planes hold 2 X)
+    const float hsc = f16 ? d.tc_inv_scale[b] : 1.f;
     const int ch = b / d.tc_KC, q = b - ch * d.tc_KC;
     const int64_t jr = (int64_t)ch * d.tc_N + q, ji = jr + d.tc_KC;
     const int64_t row_el = (int64_t)d.out_cols * Nf;   // bf16 per B row
@@ -979,12 +989,12 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   const Kc inv_L{d.inv_L, d.inv_L_hi, d.inv_L_lo};
   // range scaling: outputs of right-hand side b times 2^(e_b + out_exp), in two
   // exact steps (each factor a normal double; the product may not be)
-  const bool scaled = d.rhs_absmax != nullptr;
+  const int oexp = d.rhs_absmax != nullptr ? range_exp(d.rhs_absmax[b]) + d.out_exp : 0;
+  const bool scaled = oexp != 0;
   double s1 = 1.0, s2 = 1.0;
   if (scaled) {
-    const int e = range_exp(d.rhs_absmax[b]) + d.out_exp;
-    s1 = ldexp(1.0, e / 2);
-    s2 = ldexp(1.0, e - e / 2);
+    s1 = ldexp(1.0, oexp / 2);
+    s2 = ldexp(1.0, oexp - oexp / 2);
   }
   auto gdst = [&](int t, int p, int, C v) {
     const int c = c0 + 2 * p;
@@ -1071,50 +1081,6 @@ int fft_pairs_for_grid(int L, Groups groups) {
     while (np > 1 && groups(np) < sms) np /= 2;
   }
   return np;
-}
-
-template <typename Tin, typename P>
-cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
-  // the tensor-core B planes are written 8 channels (4 pairs) at a time
-  const int np = d.fmt == FMT_TC ? fft_pairs<P>(d.plan.L)
-                                 : fft_pairs_for_grid<P>(d.plan.L, [&](int n) {
-                                     return (int64_t)d.rows * ((d.out_cols + 2 * n - 1) / (2 * n)) * d.K;
-                                   });
-  if (np == fft_pairs<P>(d.plan.L)) {
-    switch (d.plan.L) {
-#define FFTMV_CASE(LL) \
-  case LL: return fwd_launch_np<Tin, P, fft_pairs<P>(LL), LL>(d, s);
-      FFTMV_FIXED_LENGTHS(FFTMV_CASE)
-#undef FFTMV_CASE
-      default: break;
-    }
-  }
-  switch (np) {
-    case 8: return fwd_launch_np<Tin, P, 8, 0>(d, s);
-    case 4: return fwd_launch_np<Tin, P, 4, 0>(d, s);
-    case 2: return fwd_launch_np<Tin, P, 2, 0>(d, s);
-    default: return fwd_launch_np<Tin, P, 1, 0>(d, s);
-  }
-}
-
-template <typename P, typename Tout>
-cudaError_t inv_launch(const InvDesc& d, cudaStream_t s) {
-  const int np = fft_pairs_for_grid<P>(d.plan.L, [&](int n) { return (int64_t)((d.cols + 2 * n - 1) / (2 * n)) * d.K; });
-  if (np == fft_pairs<P>(d.plan.L)) {
-    switch (d.plan.L) {
-#define FFTMV_CASE(LL) \
-  case LL: return inv_launch_np<P, Tout, fft_pairs<P>(LL), LL>(d, s);
-      FFTMV_FIXED_LENGTHS(FFTMV_CASE)
-#undef FFTMV_CASE
-      default: break;
-    }
-  }
-  switch (np) {
-    case 8: return inv_launch_np<P, Tout, 8, 0>(d, s);
-    case 4: return inv_launch_np<P, Tout, 4, 0>(d, s);
-    case 2: return inv_launch_np<P, Tout, 2, 0>(d, s);
-    default: return inv_launch_np<P, Tout, 1, 0>(d, s);
-  }
 }
 
 }  // namespace

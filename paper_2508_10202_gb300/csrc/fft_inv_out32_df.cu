@@ -1,6 +1,6 @@
 // Inverse FFTs, df arithmetic, float output: one instantiation unit of
 // fft_core.cuh (the units compile in parallel).
-#include "fft_core.cuh"
+#include "fft_launch.cuh"
 
 namespace fftmv {
 cudaError_t launch_irfft_inv_df_float(const InvDesc& d, cudaStream_t s) { return inv_launch<DFP, float>(d, s); }

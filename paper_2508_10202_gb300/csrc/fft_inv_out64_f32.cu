@@ -1,6 +1,6 @@
 // Inverse FFTs, f32 arithmetic, double output: one instantiation unit of
 // fft_core.cuh (the units compile in parallel).
-#include "fft_core.cuh"
+#include "fft_launch.cuh"
 
 namespace fftmv {
 cudaError_t launch_irfft_inv_f32_double(const InvDesc& d, cudaStream_t s) { return inv_launch<float, double>(d, s); }

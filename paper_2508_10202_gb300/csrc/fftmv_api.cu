@@ -120,6 +120,7 @@ struct fftmv_op {
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
   float4* twdf = nullptr;     // twiddles as FP32 hi/lo pairs
+  float2* twdif32 = nullptr;  // twiddle table of the length's DifPlan (FP32), when it has one
   double2* fhat64 = nullptr;  // master F-hat [Nf][Nd][ldn], FP64
   float4* fhat_df = nullptr;  // FP32 hi/lo pairs
   float2* fhat32 = nullptr;   // FP32
@@ -197,6 +198,7 @@ void release(fftmv_op* op) {
   cudaFree(op->tw64);
   cudaFree(op->tw32);
   cudaFree(op->twdf);
+  cudaFree(op->twdif32);
   cudaFree(op->fhat64);
   cudaFree(op->fhat_df);
   cudaFree(op->fhat32);
@@ -290,6 +292,7 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   f.X_ld_b = op->Nf * c.in_ld;
   f.fmt = c.in_fmt;
   f.pad_single = p.pad == FFTMV_F32;
+  f.twd = fprec == FFT_F32 ? op->twdif32 : nullptr;
   {
     const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
     f.pair_ok = (reinterpret_cast<uintptr_t>(x) % (2 * esz) == 0) && f.x_ld_t % 2 == 0 && f.x_ld_b % 2 == 0;
@@ -377,6 +380,11 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     v.inv_L = 1.0 / (double)op->L;
     v.inv_L_hi = (float)v.inv_L;
     v.inv_L_lo = (float)(v.inv_L - (double)v.inv_L_hi);
+    v.twd = iprec == FFT_F32 ? op->twdif32 : nullptr;
+    {
+      const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
+      v.out_pair_ok = reinterpret_cast<uintptr_t>(y) % (2 * esz) == 0 && v.y_ld_t % 2 == 0 && v.y_ld_b % 2 == 0;
+    }
     v.rhs_absmax = absmax;
     // FP64 spectra of the native block matvec come back to the double-float
     // range before the inverse; F-hat's exponent returns at the unpad
@@ -566,6 +574,25 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
   if ((rc = cu(cudaMemcpy(op->tw32, tw32.data(), L * sizeof(float2), cudaMemcpyHostToDevice), "twiddle copy"))) return rc;
   if ((rc = cu(cudaMalloc(&op->twdf, L * sizeof(float4)), "cudaMalloc(twiddles)"))) return rc;
   if ((rc = cu(cudaMemcpy(op->twdf, twdf.data(), L * sizeof(float4), cudaMemcpyHostToDevice), "twiddle copy"))) return rc;
+  if (dif_plan((int)L).n > 0) {
+    // rows of W_{M_s}^{j q} = exp(-2 pi i (L / M_s) j q / L) per pass with S_s > 1
+    const DifPlan pl = dif_plan((int)L);
+    std::vector<float2> twd((size_t)dif_tw_size((int)L), make_float2(1.f, 0.f));
+    for (int sp = 0; sp < pl.n; ++sp) {
+      const int M = dif_M((int)L, sp), S = dif_S((int)L, sp), R = pl.rad[sp];
+      if (S == 1) continue;
+      for (int j = 0; j < S; ++j)
+        for (int q = 1; q < R; ++q) {
+          const long double a = -2.0L * 3.141592653589793238462643383279502884L * (long double)(j * q) / (long double)M;
+          twd[(size_t)dif_tw_offset((int)L, sp) + (size_t)j * dif_tw_row(R) + (q - 1)] =
+              make_float2((float)cosl(a), (float)sinl(a));
+        }
+    }
+    if ((rc = cu(cudaMalloc(&op->twdif32, twd.size() * sizeof(float2)), "cudaMalloc(twiddles)"))) return rc;
+    if ((rc = cu(cudaMemcpy(op->twdif32, twd.data(), twd.size() * sizeof(float2), cudaMemcpyHostToDevice),
+                 "twiddle copy")))
+      return rc;
+  }
 
   if ((rc = cu(cudaMalloc(&op->status, sizeof(unsigned int)), "cudaMalloc(status)"))) return rc;
   if ((rc = cu(cudaMemset(op->status, 0, sizeof(unsigned int)), "cudaMemset(status)"))) return rc;

@@ -46,6 +46,43 @@ struct FftPlan {
   unsigned magic[kMaxPasses]; // ceil(2^32 / ns): j / ns = umulhi(j, magic) for j < 2^16 (ns > 1)
 };
 
+// In-place decimation-in-frequency plans of the compile-time FFT lengths
+// (the FP32 kernels of fft_dif.cuh).  L = rad[0] rad[1] ... rad[n-1]; pass s
+// works on blocks of M_s = L / (rad[0] ... rad[s-1]) points with butterflies
+// of stride S_s = M_s / rad[s], and multiplies output q of butterfly j by
+// W_{M_s}^{j q} (W_M = exp(-2 pi i / M)).  The result is left in
+// digit-reversed order: frequency r_0 + rad[0] (r_1 + rad[1] (r_2 ...)) at
+// position r_0 S_0 + r_1 S_1 + r_2 S_2 ...
+struct DifPlan {
+  int n;
+  int rad[4];
+};
+__host__ __device__ constexpr DifPlan dif_plan(int L) {
+  return L == 2000 ? DifPlan{3, {16, 5, 25, 1}}
+       : L == 1000 ? DifPlan{3, {8, 5, 25, 1}}
+       : L == 512  ? DifPlan{3, {8, 8, 8, 1}}
+       : L == 256  ? DifPlan{2, {16, 16, 1, 1}}
+       : L == 128  ? DifPlan{2, {16, 8, 1, 1}}
+                   : DifPlan{0, {1, 1, 1, 1}};
+}
+__host__ __device__ constexpr int dif_M(int L, int s) {
+  int m = L;
+  for (int i = 0; i < s; ++i) m /= dif_plan(L).rad[i];
+  return m;
+}
+__host__ __device__ constexpr int dif_S(int L, int s) { return dif_M(L, s) / dif_plan(L).rad[s]; }
+// twiddle table of the plan: for every pass with S_s > 1, S_s rows of
+// rad[s] - 1 entries (W_{M_s}^{j q}, q = 1 .. rad[s] - 1) padded to an even
+// count, so that rows start 16-byte aligned for FP32 complexes
+__host__ __device__ constexpr int dif_tw_row(int R) { return R / 2 * 2; }
+__host__ __device__ constexpr int dif_tw_offset(int L, int s) {
+  int off = 0;
+  for (int i = 0; i < s; ++i)
+    if (dif_S(L, i) > 1) off += dif_S(L, i) * dif_tw_row(dif_plan(L).rad[i]);
+  return off;
+}
+__host__ __device__ constexpr int dif_tw_size(int L) { return dif_tw_offset(L, dif_plan(L).n); }
+
 // Forward real FFT of zero-padded channels (phases 1-2 fused).
 // Channel c = (row, col) with col < cols; channels (2q, 2q+1) of a row are
 // transformed together as one complex signal.  x[b][t][row][col] is read for
@@ -71,6 +108,7 @@ struct FwdDesc {
   // bits of max |x_b| as a double; the kernel divides right-hand side b by the
   // power of two 2^e_b, e_b = range_exp(in_absmax[b]), as it loads it.
   const unsigned long long* in_absmax;
+  const void* twd;         // twiddle table of the length's DifPlan (FP32 complexes), or null
 };
 
 // Inverse real FFT of Hermitian half spectra followed by unpad (phases 4-5 fused).
@@ -96,6 +134,8 @@ struct InvDesc {
   // the output cast).
   const unsigned long long* rhs_absmax;
   int mid_exp, out_exp;
+  const void* twd;         // twiddle table of the length's DifPlan (FP32 complexes), or null
+  int out_pair_ok;         // y and its strides allow storing channels (c, c+1) as one vector
 };
 
 // Per-frequency block matvec (phase 3) for K right-hand sides.
@@ -156,14 +196,18 @@ cudaError_t launch_convert_fhat(int kind, const double2* master, void* out, size
 // of max |x| over the n values of right-hand side b (double or float input),
 // as a double; the caller zeroes it first.
 cudaError_t launch_absmax(const void* x, bool x_f32, int K, int64_t n, unsigned long long* absmax, cudaStream_t s);
-// the exponent e with max / 2^e in [1, 2) for the bits of a non-negative
-// double max; 0 for zero, -1022 for subnormals, 1023 for inf and NaN
+// The scaling exponent for the bits of a non-negative double max: 0 while
+// max / 2^0 lies in [2^-40, 2^41) (data that need no scaling: F-hat and inputs
+// both within it keep every double-float intermediate of an Nt, Nm <= 2^20
+// operator inside FP32's range, products and lo parts included, so the common
+// case runs unscaled and bit for bit as without this mechanism); otherwise e
+// with max / 2^e in [1, 2): -1022 for subnormals, 1023 for inf and NaN.
+constexpr int kRangeFreeExp = 40;
 __host__ __device__ inline int range_exp(unsigned long long bits) {
   const int biased = (int)((bits >> 52) & 0x7FF);
   if (bits == 0) return 0;
-  if (biased == 0) return -1022;
-  if (biased == 0x7FF) return 1023;
-  return biased - 1023;
+  const int e = biased == 0 ? -1022 : biased == 0x7FF ? 1023 : biased - 1023;
+  return (e >= -kRangeFreeExp && e <= kRangeFreeExp) ? 0 : e;
 }
 
 int fft_max_length(int prec);

@@ -11,7 +11,9 @@
 // result).  The FP16 mode splits the same way into FP16 (11-bit) parts after
 // exact power-of-two scaling: F-hat_w by s_w (per frequency), the spectra of
 // right-hand side b by s_b; both operands of one MMA are then FP16, and the
-// epilogue multiplies each output by s_w * s_b.
+// epilogue multiplies each output by s_w * s_b.  The FFT hands over its
+// spectra doubled (the real-to-complex split's 1/2 is left out there), so the
+// epilogue also halves every output.
 //
 // Complex arithmetic without duplicating data: A is four planes
 // (Re hi, Re lo, Im hi, Im lo) of F-hat_w, B is [Re X | Im X] (2*KC columns,
@@ -376,7 +378,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int q = qlo + c * 16 + i;
             const int b = ch * KC + q;
             if (c * 16 + i < qn && b < a.K) {
-              const float sc = a.a_scale ? sw * a.b_scale[b] : 1.f;   // powers of two: exact
+              // the FFT writes 2 X (the split's 1/2 lands here); powers of two: exact
+              const float sc = a.a_scale ? 0.5f * sw * a.b_scale[b] : 0.5f;
               a.y[b * a.y_ld_b + (int64_t)w * a.y_ld_w + row] = make_float2(sre[c * 16 + i] * sc, sim[c * 16 + i] * sc);
             }
           }
