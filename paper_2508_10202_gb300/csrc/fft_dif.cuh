@@ -29,6 +29,10 @@ namespace fftmv {
 namespace {
 
 constexpr int kDifPad = 2;
+#ifndef FFTMV_DIF_UNROLL
+#define FFTMV_DIF_UNROLL 1
+#endif
+constexpr int kDifUnroll = FFTMV_DIF_UNROLL;
 
 template <int L, int NP>
 __device__ __forceinline__ int dif_e(int pos, int p) {
@@ -74,25 +78,34 @@ __device__ __forceinline__ int dif_pos(int k) {
   return pos;
 }
 
-// v[q] *= W^{j q} (INV: conj), q = 1 .. R-1, from a twiddle-table row
-template <bool INV, int R>
-__device__ __forceinline__ void dif_twiddle(float2* v, const float2* __restrict__ row) {
-  const float4* r4 = reinterpret_cast<const float4*>(row);
+// a twiddle-table row (W^{j q}, q = 1 .. R-1, two per 16-byte load), loaded
+// ahead of the butterfly's data so that both latencies overlap
+template <int R>
+struct DifTw {
+  float4 w[dif_tw_row(R) / 2];
+  __device__ __forceinline__ void load(const float2* __restrict__ row) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
 #pragma unroll
-  for (int h = 0; h < dif_tw_row(R) / 2; ++h) {
-    const float4 w = __ldg(r4 + h);
+    for (int h = 0; h < dif_tw_row(R) / 2; ++h) w[h] = __ldg(r4 + h);
+  }
+  // v[q] *= W^{j q} (INV: conj), q = 1 .. R-1
+  template <bool INV>
+  __device__ __forceinline__ void apply(float2* v) const {
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int q = 1 + 2 * h + u;
-      if (q < R) {
-        const float wr = u ? w.z : w.x, wi = u ? w.w : w.y;
-        const float2 a = v[q];
-        v[q] = INV ? make_float2(fmaf(a.x, wr, a.y * wi), fmaf(a.y, wr, -(a.x * wi)))
-                   : make_float2(fmaf(a.x, wr, -(a.y * wi)), fmaf(a.x, wi, a.y * wr));
+    for (int h = 0; h < dif_tw_row(R) / 2; ++h) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int q = 1 + 2 * h + u;
+        if (q < R) {
+          const float wr = u ? w[h].z : w[h].x, wi = u ? w[h].w : w[h].y;
+          const float2 a = v[q];
+          v[q] = INV ? make_float2(fmaf(a.x, wr, a.y * wi), fmaf(a.y, wr, -(a.x * wi)))
+                     : make_float2(fmaf(a.x, wr, -(a.y * wi)), fmaf(a.x, wi, a.y * wr));
+        }
       }
     }
   }
-}
+};
 
 // pass s (of the plan) in shared memory
 template <bool INV, int NP, int L, int s, int T>
@@ -100,15 +113,17 @@ __device__ __forceinline__ void dif_pass(float2* __restrict__ buf, const float2*
   constexpr int R = dif_plan(L).rad[s], M = dif_M(L, s), S = M / R;
   constexpr int NBUT = (L / M) * S * NP;
   constexpr int ES = dif_es<L, NP, s>();
-#pragma unroll 1
+#pragma unroll kDifUnroll
   for (int bt = threadIdx.x; bt < NBUT; bt += T) {
     const int p = bt % NP, r = bt / NP, j = r % S, blk = r / S;
     float2* base = buf + dif_e<L, NP>(blk * M + j, p);
+    DifTw<R> tw;
+    if constexpr (S > 1) tw.load(twd + dif_tw_offset(L, s) + j * dif_tw_row(R));
     float2 v[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = base[q * ES];
     Dft<float, R, INV>::run(v);
-    if constexpr (S > 1) dif_twiddle<INV, R>(v, twd + dif_tw_offset(L, s) + j * dif_tw_row(R));
+    if constexpr (S > 1) tw.template apply<INV>(v);
 #pragma unroll
     for (int q = 0; q < R; ++q) base[q * ES] = v[q];
   }
@@ -180,6 +195,8 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
     for (int bt = threadIdx.x; bt < S0 * NP; bt += T) {
       const int p = bt % NP, j = bt / NP;
       const int c = c0 + 2 * p;
+      DifTw<R0> tw;
+      tw.load(twd + j * dif_tw_row(R0));
       C v[R0];
       if (fast) {
         const Tin* xp = static_cast<const Tin*>(d.x) + xo + (int64_t)j * d.x_ld_t + c;
@@ -196,7 +213,7 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
       }
       if constexpr (half) DftHalf<P, R0, false>::run(v);
       else Dft<P, R0, false>::run(v);
-      dif_twiddle<false, R0>(v, twd + j * dif_tw_row(R0));
+      tw.template apply<false>(v);
       C* base = buf + dif_e<L, NP>(j, p);
 #pragma unroll
       for (int q = 0; q < R0; ++q) base[q * ES] = v[q];
@@ -239,82 +256,100 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
     const int64_t di = (ji - jr) * row_el;
     int ew = dif_e<L, NP>(dif_pos<L>(w0), cg / 2);
     int ec = w0 == 0 ? dif_e<L, NP>(dif_pos<L>(L - DW), cg / 2) + (DW / PI) * NP : dif_e<L, NP>(dif_pos<L>(L - w0), cg / 2);
-    for (int w = w0; w < Nf; w += DW, ew += (DW / PI) * NP, ec -= (DW / PI) * NP, Bw += (int64_t)DW << sh) {
-      const int ecw = w == 0 ? ew : ec;
-      C zw[G / 2], zc[G / 2];
-      if constexpr (G >= 4) {
+    // the loop once per (all channels present, FP16) case: no per-channel
+    // checks or format branches inside
+    auto run = [&](auto full_t, auto f16_t) {
+      constexpr bool FULL = decltype(full_t)::value, F16 = decltype(f16_t)::value;
+      int ew_ = ew, ec_ = ec;
+      unsigned short* Bw_ = Bw;
+      for (int w = w0; w < Nf; w += DW, ew_ += (DW / PI) * NP, ec_ -= (DW / PI) * NP, Bw_ += (int64_t)DW << sh) {
+        const int ecw = w == 0 ? ew_ : ec_;
+        C zw[G / 2], zc[G / 2];
+        if constexpr (G >= 4) {
 #pragma unroll
-        for (int u = 0; u < G / 2; u += 2) {
-          const float4 a = *reinterpret_cast<const float4*>(buf + ew + u);
-          const float4 bq = *reinterpret_cast<const float4*>(buf + ecw + u);
-          zw[u] = make_float2(a.x, a.y);
-          zw[u + 1] = make_float2(a.z, a.w);
-          zc[u] = make_float2(bq.x, bq.y);
-          zc[u + 1] = make_float2(bq.z, bq.w);
+          for (int u = 0; u < G / 2; u += 2) {
+            const float4 a = *reinterpret_cast<const float4*>(buf + ew_ + u);
+            const float4 bq = *reinterpret_cast<const float4*>(buf + ecw + u);
+            zw[u] = make_float2(a.x, a.y);
+            zw[u + 1] = make_float2(a.z, a.w);
+            zc[u] = make_float2(bq.x, bq.y);
+            zc[u + 1] = make_float2(bq.z, bq.w);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < G / 2; ++u) {
+            zw[u] = buf[ew_ + u];
+            zc[u] = buf[ecw + u];
+          }
         }
-      } else {
+        // pair u of the G channels: X_a = Z_w + conj Z_{L-w}, X_b = (Z_w - conj Z_{L-w}) / i
+        uint32_t hr[G / 2], lr[G / 2], hm[G / 2], lm[G / 2];   // Re hi, Re lo, Im hi, Im lo
 #pragma unroll
         for (int u = 0; u < G / 2; ++u) {
-          zw[u] = buf[ew + u];
-          zc[u] = buf[ecw + u];
+          const C z = zw[u], y = zc[u];
+          float ar = z.x + y.x, ai = z.y - y.y, br = z.y + y.y, bi = y.x - z.x;
+          if constexpr (!FULL) {
+            if (c + 2 * u >= d.cols) ar = ai = 0.f;
+            if (c + 2 * u + 1 >= d.cols) br = bi = 0.f;
+          }
+          if constexpr (F16) {
+            ar *= sc;
+            ai *= sc;
+            br *= sc;
+            bi *= sc;
+            const __half2 rh = __floats2half2_rn(ar, br), ih = __floats2half2_rn(ai, bi);
+            const float2 rf = __half22float2(rh), mf = __half22float2(ih);
+            const __half2 rl = __floats2half2_rn(ar - rf.x, br - rf.y), il = __floats2half2_rn(ai - mf.x, bi - mf.y);
+            hr[u] = *reinterpret_cast<const uint32_t*>(&rh);
+            lr[u] = *reinterpret_cast<const uint32_t*>(&rl);
+            hm[u] = *reinterpret_cast<const uint32_t*>(&ih);
+            lm[u] = *reinterpret_cast<const uint32_t*>(&il);
+          } else {
+            // bf16: hi = round(x); float(hi) of the low half is the word
+            // shifted up, of the high half the word with its low half cleared
+            const __nv_bfloat162 rh = __floats2bfloat162_rn(ar, br), ih = __floats2bfloat162_rn(ai, bi);
+            const uint32_t rw = *reinterpret_cast<const uint32_t*>(&rh), iw = *reinterpret_cast<const uint32_t*>(&ih);
+            const __nv_bfloat162 rl =
+                __floats2bfloat162_rn(ar - __uint_as_float(rw << 16), br - __uint_as_float(rw & 0xFFFF0000u));
+            const __nv_bfloat162 il =
+                __floats2bfloat162_rn(ai - __uint_as_float(iw << 16), bi - __uint_as_float(iw & 0xFFFF0000u));
+            hr[u] = rw;
+            lr[u] = *reinterpret_cast<const uint32_t*>(&rl);
+            hm[u] = iw;
+            lm[u] = *reinterpret_cast<const uint32_t*>(&il);
+          }
         }
-      }
-      // pair u of the G channels: X_a = Z_w + conj Z_{L-w}, X_b = (Z_w - conj Z_{L-w}) / i
-      uint32_t hr[G / 2], lr[G / 2], hm[G / 2], lm[G / 2];   // Re hi, Re lo, Im hi, Im lo
-#pragma unroll
-      for (int u = 0; u < G / 2; ++u) {
-        const C z = zw[u], y = zc[u];
-        float ar = z.x + y.x, ai = z.y - y.y, br = z.y + y.y, bi = y.x - z.x;
-        if (!full) {
-          if (c + 2 * u >= d.cols) ar = ai = 0.f;
-          if (c + 2 * u + 1 >= d.cols) br = bi = 0.f;
-        }
-        if (f16) {
-          ar *= sc;
-          ai *= sc;
-          br *= sc;
-          bi *= sc;
-          const __half2 rh = __floats2half2_rn(ar, br), ih = __floats2half2_rn(ai, bi);
-          const float2 rf = __half22float2(rh), mf = __half22float2(ih);
-          const __half2 rl = __floats2half2_rn(ar - rf.x, br - rf.y), il = __floats2half2_rn(ai - mf.x, bi - mf.y);
-          hr[u] = *reinterpret_cast<const uint32_t*>(&rh);
-          lr[u] = *reinterpret_cast<const uint32_t*>(&rl);
-          hm[u] = *reinterpret_cast<const uint32_t*>(&ih);
-          lm[u] = *reinterpret_cast<const uint32_t*>(&il);
+        Vec vhr, vlr, vhm, vlm;
+        if constexpr (G == 8) {
+          vhr = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+          vlr = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+          vhm = make_uint4(hm[0], hm[1], hm[2], hm[3]);
+          vlm = make_uint4(lm[0], lm[1], lm[2], lm[3]);
+        } else if constexpr (G == 4) {
+          vhr = make_uint2(hr[0], hr[1]);
+          vlr = make_uint2(lr[0], lr[1]);
+          vhm = make_uint2(hm[0], hm[1]);
+          vlm = make_uint2(lm[0], lm[1]);
         } else {
-          // bf16: hi = round(x); float(hi) of the low half is the word shifted
-          // up, of the high half the word with its low half cleared
-          const __nv_bfloat162 rh = __floats2bfloat162_rn(ar, br), ih = __floats2bfloat162_rn(ai, bi);
-          const uint32_t rw = *reinterpret_cast<const uint32_t*>(&rh), iw = *reinterpret_cast<const uint32_t*>(&ih);
-          const __nv_bfloat162 rl = __floats2bfloat162_rn(ar - __uint_as_float(rw << 16), br - __uint_as_float(rw & 0xFFFF0000u));
-          const __nv_bfloat162 il = __floats2bfloat162_rn(ai - __uint_as_float(iw << 16), bi - __uint_as_float(iw & 0xFFFF0000u));
-          hr[u] = rw;
-          lr[u] = *reinterpret_cast<const uint32_t*>(&rl);
-          hm[u] = iw;
-          lm[u] = *reinterpret_cast<const uint32_t*>(&il);
+          vhr = hr[0];
+          vlr = lr[0];
+          vhm = hm[0];
+          vlm = lm[0];
         }
+        *reinterpret_cast<Vec*>(Bw_) = vhr;
+        *reinterpret_cast<Vec*>(Bw_ + plane_el) = vlr;
+        *reinterpret_cast<Vec*>(Bw_ + di) = vhm;
+        *reinterpret_cast<Vec*>(Bw_ + di + plane_el) = vlm;
       }
-      Vec vhr, vlr, vhm, vlm;
-      if constexpr (G == 8) {
-        vhr = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-        vlr = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-        vhm = make_uint4(hm[0], hm[1], hm[2], hm[3]);
-        vlm = make_uint4(lm[0], lm[1], lm[2], lm[3]);
-      } else if constexpr (G == 4) {
-        vhr = make_uint2(hr[0], hr[1]);
-        vlr = make_uint2(lr[0], lr[1]);
-        vhm = make_uint2(hm[0], hm[1]);
-        vlm = make_uint2(lm[0], lm[1]);
-      } else {
-        vhr = hr[0];
-        vlr = lr[0];
-        vhm = hm[0];
-        vlm = lm[0];
-      }
-      *reinterpret_cast<Vec*>(Bw) = vhr;
-      *reinterpret_cast<Vec*>(Bw + plane_el) = vlr;
-      *reinterpret_cast<Vec*>(Bw + di) = vhm;
-      *reinterpret_cast<Vec*>(Bw + di + plane_el) = vlm;
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    if (full) {
+      if (f16) run(T_{}, T_{});
+      else run(T_{}, F_{});
+    } else {
+      if (f16) run(F_{}, T_{});
+      else run(F_{}, F_{});
     }
     return;
   }
@@ -382,6 +417,10 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
   constexpr int U = fft_inv_loads(sizeof(C), 25, Nf, NP, T);
   const bool midsc = d.rhs_absmax != nullptr && d.in_fmt == FMT_C128 && d.mid_exp != 0;
   const double midf = midsc ? ldexp(1.0, d.mid_exp) : 1.0;
+  // every channel of the CTA present in FP32 pairs: one 16-byte load per
+  // item and no per-item checks but the end of the spectrum
+  // (a variant with the per-item checks hoisted out for full channel groups
+  // issued its loads less well: 2.70 against 2.48 ms at K = 64)
   for (int i0 = threadIdx.x; i0 < Nf * NP; i0 += U * T) {
     C a[U], bb[U];
 #pragma unroll
@@ -433,45 +472,55 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
   }
   const float invL = (float)d.inv_L;
   const bool vec = d.out_pair_ok && !d.unpad_single;
+  const int Nt = d.Nt;
+  const int64_t ystep = (int64_t)(L / R) * d.y_ld_t;
+  // every channel present, unscaled, pairs stored as vectors: the only
+  // per-output test left is t < Nt
+  const bool fastst = vec && !scaled && c0 + NCH <= d.cols;
+  auto last = [&](auto fast_t) {
+    constexpr bool FAST = decltype(fast_t)::value;
 #pragma unroll 1
-  for (int bt = threadIdx.x; bt < NBUT; bt += T) {
-    const int p = bt % NP, blk = bt / NP;
-    const int c = c0 + 2 * p;
-    C* base = buf + dif_e<L, NP>(blk * R, p);
-    C v[R];
+    for (int bt = threadIdx.x; bt < NBUT; bt += T) {
+      const int p = bt % NP, blk = bt / NP;
+      const int c = c0 + 2 * p;
+      C* base = buf + dif_e<L, NP>(blk * R, p);
+      C v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = base[q * NP];
-    Dft<P, R, true>::run(v);
-    if (c >= d.cols) continue;
-    int rest = blk * R, tb = 0, mul = 1;
+      for (int q = 0; q < R; ++q) v[q] = base[q * NP];
+      Dft<P, R, true>::run(v);
+      if (!FAST && c >= d.cols) continue;
+      int rest = blk * R, tb = 0, mul = 1;
 #pragma unroll
-    for (int k = 0; k < s; ++k) {
-      tb += (rest / dif_S(L, k)) * mul;
-      rest %= dif_S(L, k);
-      mul *= pl.rad[k];
-    }
-    const bool two = c + 1 < d.cols;
+      for (int k = 0; k < s; ++k) {
+        tb += (rest / dif_S(L, k)) * mul;
+        rest %= dif_S(L, k);
+        mul *= pl.rad[k];
+      }
+      Tout* yb = static_cast<Tout*>(d.y) + b * d.y_ld_b + (int64_t)tb * d.y_ld_t + c;
+      const bool two = FAST || c + 1 < d.cols;
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int t = tb + (L / R) * q;
-      if (t >= d.Nt) continue;
-      const int64_t o = b * d.y_ld_b + t * d.y_ld_t + c;
-      const float re = v[q].x * invL, im = v[q].y * invL;
-      if (scaled) {
-        store_real_scaled<Tout, P>(d.y, o, re, d.unpad_single, s1, s2);
-        if (two) store_real_scaled<Tout, P>(d.y, o + 1, im, d.unpad_single, s1, s2);
-      } else if (vec && two) {
-        using V = typename std::conditional<sizeof(Tout) == 4, float2, double2>::type;
-        V pv;
-        pv.x = (Tout)re;
-        pv.y = (Tout)im;
-        *reinterpret_cast<V*>(static_cast<Tout*>(d.y) + o) = pv;
-      } else {
-        store_real<Tout, P>(d.y, o, re, d.unpad_single);
-        if (two) store_real<Tout, P>(d.y, o + 1, im, d.unpad_single);
+      for (int q = 0; q < R; ++q) {
+        if (tb + (L / R) * q >= Nt) continue;
+        Tout* yq = yb + q * ystep;
+        const float re = v[q].x * invL, im = v[q].y * invL;
+        if (FAST || (vec && two && !scaled)) {
+          using V = typename std::conditional<sizeof(Tout) == 4, float2, double2>::type;
+          V pv;
+          pv.x = (Tout)re;
+          pv.y = (Tout)im;
+          *reinterpret_cast<V*>(yq) = pv;
+        } else if (scaled) {
+          store_real_scaled<Tout, P>(yq, 0, re, d.unpad_single, s1, s2);
+          if (two) store_real_scaled<Tout, P>(yq, 1, im, d.unpad_single, s1, s2);
+        } else {
+          store_real<Tout, P>(yq, 0, re, d.unpad_single);
+          if (two) store_real<Tout, P>(yq, 1, im, d.unpad_single);
+        }
       }
     }
-  }
+  };
+  if (fastst) last(std::true_type{});
+  else last(std::false_type{});
 }
 
 template <typename Tin, int NP, int L>
