@@ -419,8 +419,9 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
   const double midf = midsc ? ldexp(1.0, d.mid_exp) : 1.0;
   // every channel of the CTA present in FP32 pairs: one 16-byte load per
   // item and no per-item checks but the end of the spectrum
-  // (a variant with the per-item checks hoisted out for full channel groups
-  // issued its loads less well: 2.70 against 2.48 ms at K = 64)
+  // (two variants that issue the pair loads without the per-item branches,
+  // checks hoisted out or indices clamped, were slower: 2.70 against 2.48 ms
+  // at K = 64)
   for (int i0 = threadIdx.x; i0 < Nf * NP; i0 += U * T) {
     C a[U], bb[U];
 #pragma unroll
@@ -471,56 +472,48 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
     s2 = ldexp(1.0, oexp - oexp / 2);
   }
   const float invL = (float)d.inv_L;
-  const bool vec = d.out_pair_ok && !d.unpad_single;
+  const bool vec = d.out_pair_ok && !d.unpad_single && !scaled;
   const int Nt = d.Nt;
   const int64_t ystep = (int64_t)(L / R) * d.y_ld_t;
-  // every channel present, unscaled, pairs stored as vectors: the only
-  // per-output test left is t < Nt
-  const bool fastst = vec && !scaled && c0 + NCH <= d.cols;
-  auto last = [&](auto fast_t) {
-    constexpr bool FAST = decltype(fast_t)::value;
 #pragma unroll 1
-    for (int bt = threadIdx.x; bt < NBUT; bt += T) {
-      const int p = bt % NP, blk = bt / NP;
-      const int c = c0 + 2 * p;
-      C* base = buf + dif_e<L, NP>(blk * R, p);
-      C v[R];
+  for (int bt = threadIdx.x; bt < NBUT; bt += T) {
+    const int p = bt % NP, blk = bt / NP;
+    const int c = c0 + 2 * p;
+    C* base = buf + dif_e<L, NP>(blk * R, p);
+    C v[R];
 #pragma unroll
-      for (int q = 0; q < R; ++q) v[q] = base[q * NP];
-      Dft<P, R, true>::run(v);
-      if (!FAST && c >= d.cols) continue;
-      int rest = blk * R, tb = 0, mul = 1;
+    for (int q = 0; q < R; ++q) v[q] = base[q * NP];
+    Dft<P, R, true>::run(v);
+    if (c >= d.cols) continue;
+    int rest = blk * R, tb = 0, mul = 1;
 #pragma unroll
-      for (int k = 0; k < s; ++k) {
-        tb += (rest / dif_S(L, k)) * mul;
-        rest %= dif_S(L, k);
-        mul *= pl.rad[k];
-      }
-      Tout* yb = static_cast<Tout*>(d.y) + b * d.y_ld_b + (int64_t)tb * d.y_ld_t + c;
-      const bool two = FAST || c + 1 < d.cols;
+    for (int k = 0; k < s; ++k) {
+      tb += (rest / dif_S(L, k)) * mul;
+      rest %= dif_S(L, k);
+      mul *= pl.rad[k];
+    }
+    Tout* yb = static_cast<Tout*>(d.y) + b * d.y_ld_b + (int64_t)tb * d.y_ld_t + c;
+    const bool two = c + 1 < d.cols;
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
-        if (tb + (L / R) * q >= Nt) continue;
-        Tout* yq = yb + q * ystep;
-        const float re = v[q].x * invL, im = v[q].y * invL;
-        if (FAST || (vec && two && !scaled)) {
-          using V = typename std::conditional<sizeof(Tout) == 4, float2, double2>::type;
-          V pv;
-          pv.x = (Tout)re;
-          pv.y = (Tout)im;
-          *reinterpret_cast<V*>(yq) = pv;
-        } else if (scaled) {
-          store_real_scaled<Tout, P>(yq, 0, re, d.unpad_single, s1, s2);
-          if (two) store_real_scaled<Tout, P>(yq, 1, im, d.unpad_single, s1, s2);
-        } else {
-          store_real<Tout, P>(yq, 0, re, d.unpad_single);
-          if (two) store_real<Tout, P>(yq, 1, im, d.unpad_single);
-        }
+    for (int q = 0; q < R; ++q) {
+      if (tb + (L / R) * q >= Nt) continue;
+      Tout* yq = yb + q * ystep;
+      const float re = v[q].x * invL, im = v[q].y * invL;
+      if (vec && two) {
+        using V = typename std::conditional<sizeof(Tout) == 4, float2, double2>::type;
+        V pv;
+        pv.x = (Tout)re;
+        pv.y = (Tout)im;
+        *reinterpret_cast<V*>(yq) = pv;
+      } else if (scaled) {
+        store_real_scaled<Tout, P>(yq, 0, re, d.unpad_single, s1, s2);
+        if (two) store_real_scaled<Tout, P>(yq, 1, im, d.unpad_single, s1, s2);
+      } else {
+        store_real<Tout, P>(yq, 0, re, d.unpad_single);
+        if (two) store_real<Tout, P>(yq, 1, im, d.unpad_single);
       }
     }
-  };
-  if (fastst) last(std::true_type{});
-  else last(std::false_type{});
+  }
 }
 
 template <typename Tin, int NP, int L>
