@@ -100,7 +100,7 @@ class _Batch:
 class Server:
     def __init__(self, operators: dict[str, Operator], budget_bytes: int, n_streams: int = 4,
                  max_batch_rhs: int = 64, precision: dict | None = None, graphs: bool = True,
-                 keep_outputs: bool = True):
+                 keep_outputs: bool = True, policy: str = "fifo", starve_ms: float = 20.0):
         if not operators:
             raise ServerError("no operators")
         self.ops = dict(operators)
@@ -119,6 +119,15 @@ class Server:
         # False: a finished request drops its output (load generators that
         # only measure latency would otherwise hold every result in HBM)
         self.keep_outputs = keep_outputs
+        # "fifo": the oldest request that fits opens the next batch.  "fullest":
+        # the (operator, direction) with the most queued right-hand sides opens
+        # it (one pass over F-hat serves up to max_batch_rhs of them, so fuller
+        # batches raise throughput), unless the oldest request has waited
+        # starve_ms, which then goes first.
+        if policy not in ("fifo", "fullest"):
+            raise ServerError(f"unknown policy {policy!r}")
+        self.policy = policy
+        self.starve_s = starve_ms * 1e-3
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
         self.free_streams = collections.deque(range(n_streams))
         self.queue: collections.deque[Request] = collections.deque()
@@ -255,15 +264,31 @@ class Server:
         self.in_use += nbytes
         return key
 
+    def _order(self) -> list[Request]:
+        """Queued requests in the order they may open a batch."""
+        q = list(self.queue)
+        if self.policy == "fifo" or not q:
+            return q
+        if time.perf_counter() - q[0].arrival >= self.starve_s:
+            return q
+        load: dict[tuple, int] = collections.defaultdict(int)
+        for r in q:
+            load[(r.op, r.which)] += r.K
+        return sorted(q, key=lambda r: -min(load[(r.op, r.which)], self.max_batch_rhs))   # stable: oldest first
+
     def _take_batch(self) -> list[Request] | None:
-        """The oldest request that fits opens a batch; later ones for the same
-        operator and direction join while the budget and batch limit allow."""
-        for i, r in enumerate(self.queue):
+        """The first request (in policy order) that fits opens a batch; later
+        ones for the same operator and direction join while the budget and
+        batch limit allow."""
+        order = self._order()
+        for i, r in enumerate(order):
             need = self._bytes(r.op, r.which, r.K)
             if need > self.free_bytes():
                 continue
             batch, K = [r], r.K
-            for q in list(self.queue)[i + 1:]:
+            for q in self.queue:
+                if q is r:
+                    continue
                 if q.op == r.op and q.which == r.which and K + q.K <= self.max_batch_rhs:
                     if self._bytes(r.op, r.which, K + q.K) <= self.free_bytes():
                         batch.append(q)
