@@ -763,33 +763,42 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
   const int in_exp = d.in_absmax != nullptr ? range_exp(d.in_absmax[b]) : 0;
   const bool scaled = in_exp != 0;
   const double insc = scaled ? ldexp(1.0, -in_exp) : 1.0;
-  auto gsrc = [&](int t, int p, int) -> C {
-    const int c = c0 + 2 * p;
-    if (t >= d.Nt || c >= d.cols) return zero;
-    const int64_t o = xo + t * d.x_ld_t + c;
-    if (d.pair_ok && c + 1 < d.cols) {   // both channels in one 8- or 16-byte load
-      using V = typename std::conditional<sizeof(Tin) == 4, float2, double2>::type;
-      const V v = __ldg(reinterpret_cast<const V*>(static_cast<const Tin*>(d.x) + o));
-      if (scaled)
-        return A::mk(cvt_real_scaled<P, Tin>(v.x, d.pad_single, insc), cvt_real_scaled<P, Tin>(v.y, d.pad_single, insc));
-      return A::mk(cvt_real<P, Tin>(v.x, d.pad_single), cvt_real<P, Tin>(v.y, d.pad_single));
-    }
-    const Tin* xp = static_cast<const Tin*>(d.x) + o;
-    const Tin xa = __ldg(xp), xb = c + 1 < d.cols ? __ldg(xp + 1) : Tin(0);
-    if (scaled) return A::mk(cvt_real_scaled<P, Tin>(xa, d.pad_single, insc), cvt_real_scaled<P, Tin>(xb, d.pad_single, insc));
-    return A::mk(cvt_real<P, Tin>(xa, d.pad_single), cvt_real<P, Tin>(xb, d.pad_single));
+  // sample t of channel pair p, the pad cast fused; SC: range-scaled (the
+  // first pass is instantiated once per case, so the unscaled one carries no
+  // scaling code)
+  auto gsrc_of = [&](auto sc_t) {
+    constexpr bool SC = decltype(sc_t)::value;
+    return [&](int t, int p, int) -> C {
+      const int c = c0 + 2 * p;
+      if (t >= d.Nt || c >= d.cols) return zero;
+      const int64_t o = xo + t * d.x_ld_t + c;
+      if (d.pair_ok && c + 1 < d.cols) {   // both channels in one 8- or 16-byte load
+        using V = typename std::conditional<sizeof(Tin) == 4, float2, double2>::type;
+        const V v = __ldg(reinterpret_cast<const V*>(static_cast<const Tin*>(d.x) + o));
+        if constexpr (SC)
+          return A::mk(cvt_real_scaled<P, Tin>(v.x, d.pad_single, insc), cvt_real_scaled<P, Tin>(v.y, d.pad_single, insc));
+        else
+          return A::mk(cvt_real<P, Tin>(v.x, d.pad_single), cvt_real<P, Tin>(v.y, d.pad_single));
+      }
+      const Tin* xp = static_cast<const Tin*>(d.x) + o;
+      const Tin xa = __ldg(xp), xb = c + 1 < d.cols ? __ldg(xp + 1) : Tin(0);
+      if constexpr (SC)
+        return A::mk(cvt_real_scaled<P, Tin>(xa, d.pad_single, insc), cvt_real_scaled<P, Tin>(xb, d.pad_single, insc));
+      else
+        return A::mk(cvt_real<P, Tin>(xa, d.pad_single), cvt_real<P, Tin>(xb, d.pad_single));
+    };
   };
   auto sdst = [&](int, int, int e, C v) { buf[swz<C>(e)] = v; };
   auto ssrc = [&](int, int, int e) -> C { return buf[swz<C>(e)]; };
-  if constexpr (LC > 0) {
-    cpass<P, false, NP, E, LC, 0, 0, false>(T, tw, gsrc, sdst);
-    __syncthreads();
-    cpasses<P, false, NP, E, LC, 1, cplan<P>(LC).npass>(T, tw, ssrc, sdst);
-  } else {
-    any_pass<P, false, NP, E, 0, false>(d.plan, 0, tw, gsrc, sdst);
-    __syncthreads();
-    inplace_passes<P, false, NP, E>(d.plan, 1, d.plan.npass, tw, ssrc, sdst);
-  }
+  auto first = [&](auto gsrc) {
+    if constexpr (LC > 0) cpass<P, false, NP, E, LC, 0, 0, false>(T, tw, gsrc, sdst);
+    else any_pass<P, false, NP, E, 0, false>(d.plan, 0, tw, gsrc, sdst);
+  };
+  if (scaled) first(gsrc_of(std::true_type{}));
+  else first(gsrc_of(std::false_type{}));
+  __syncthreads();
+  if constexpr (LC > 0) cpasses<P, false, NP, E, LC, 1, cplan<P>(LC).npass>(T, tw, ssrc, sdst);
+  else inplace_passes<P, false, NP, E>(d.plan, 1, d.plan.npass, tw, ssrc, sdst);
 
   // split: X_a = (Z_w + conj Z_{L-w}) / 2,  X_b = (Z_w - conj Z_{L-w}) / (2i)
   auto split = [&](int w, int cc, R& xr, R& xi) {
@@ -996,20 +1005,29 @@ __global__ void __launch_bounds__(fft_bound_threads<P>(NP, LC), fft_bound_blocks
     s1 = ldexp(1.0, oexp / 2);
     s2 = ldexp(1.0, oexp - oexp / 2);
   }
-  auto gdst = [&](int t, int p, int, C v) {
-    const int c = c0 + 2 * p;
-    if (t >= d.Nt || c >= d.cols) return;
-    const int64_t o = b * d.y_ld_b + t * d.y_ld_t + c;
-    if (scaled) {
-      store_real_scaled<Tout, P>(d.y, o, A::mulk(A::re(v), inv_L), d.unpad_single, s1, s2);
-      if (c + 1 < d.cols) store_real_scaled<Tout, P>(d.y, o + 1, A::mulk(A::im(v), inv_L), d.unpad_single, s1, s2);
-      return;
-    }
-    store_real<Tout, P>(d.y, o, A::mulk(A::re(v), inv_L), d.unpad_single);
-    if (c + 1 < d.cols) store_real<Tout, P>(d.y, o + 1, A::mulk(A::im(v), inv_L), d.unpad_single);
+  // the last pass writes t < Nt straight to HBM; SC: range-scaled outputs (one
+  // instantiation of the pass per case)
+  auto gdst_of = [&](auto sc_t) {
+    constexpr bool SC = decltype(sc_t)::value;
+    return [&](int t, int p, int, C v) {
+      const int c = c0 + 2 * p;
+      if (t >= d.Nt || c >= d.cols) return;
+      const int64_t o = b * d.y_ld_b + t * d.y_ld_t + c;
+      if constexpr (SC) {
+        store_real_scaled<Tout, P>(d.y, o, A::mulk(A::re(v), inv_L), d.unpad_single, s1, s2);
+        if (c + 1 < d.cols) store_real_scaled<Tout, P>(d.y, o + 1, A::mulk(A::im(v), inv_L), d.unpad_single, s1, s2);
+      } else {
+        store_real<Tout, P>(d.y, o, A::mulk(A::re(v), inv_L), d.unpad_single);
+        if (c + 1 < d.cols) store_real<Tout, P>(d.y, o + 1, A::mulk(A::im(v), inv_L), d.unpad_single);
+      }
+    };
   };
-  if constexpr (LC > 0) cpass<P, true, NP, E, LC, cplan<P>(LC).npass - 1, 2, false>(T, tw, ssrc, gdst);
-  else any_pass<P, true, NP, E, 2, false>(d.plan, d.plan.npass - 1, tw, ssrc, gdst);
+  auto last = [&](auto gdst) {
+    if constexpr (LC > 0) cpass<P, true, NP, E, LC, cplan<P>(LC).npass - 1, 2, false>(T, tw, ssrc, gdst);
+    else any_pass<P, true, NP, E, 2, false>(d.plan, d.plan.npass - 1, tw, ssrc, gdst);
+  };
+  if (scaled) last(gdst_of(std::true_type{}));
+  else last(gdst_of(std::false_type{}));
 }
 
 template <typename K>
