@@ -169,6 +169,27 @@ def test_fixed_lengths(torch_cuda, Nt, prec, mode, fft_mode, io, K):
     op.free()
 
 
+@pytest.mark.parametrize("Nt", [64, 128, 256, 500, 1000])
+@pytest.mark.parametrize("mode,K", [("native", 5), ("bf16x2", 5), ("bf16x2", 70)])
+def test_fixed_lengths_fp32_full_groups(torch_cuda, Nt, mode, K):
+    # FP32 input whose channel groups are all full (Nm a multiple of 8) takes
+    # the pipelined forward FFT (rows staged in shared memory ahead of each
+    # tile); Nm = 200 leaves tensor-core padding columns up to 256 (zeros)
+    torch = torch_cuda
+    Nd, Nm = 5, 200
+    Fcol, m, d = make_case(Nt, Nd, Nm, K=K, seed=Nt + 1)
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", "sssss", mode)
+    m32 = m.astype(np.float32)
+    y = op.matvec(torch.from_numpy(m32).cuda()).cpu().numpy()
+    ref = oracle.matvec_direct(Fcol, m32.astype(np.float64))
+    assert oracle.rel_l2(y, ref) <= TOL32
+    for b in range(K):
+        assert oracle.rel_l2(y[b], ref[b]) <= 3 * TOL32, b
+    assert op.device_status() == 0
+    op.free()
+
+
 # --- closed forms on the GPU -------------------------------------------------
 
 @pytest.mark.parametrize("mode", ["native", "f64x2f32"])
