@@ -65,7 +65,10 @@ VARIANTS = {
     "paper_mp_optimum": (("dssdd", "native", "f64x2f32"), ("ddssd", "native", "f64x2f32")),
     "all_fp32": (("sssss", "native", "native"), ("sssss", "native", "native")),
 }
-KERNELS_PER_MATVEC = 3
+# kernels of ours per headline matvec: the range check (largest magnitude of the
+# input), the forward FFT, the block matvec and the inverse FFT (plus one
+# cudaMemsetAsync of the range check's K words)
+KERNELS_PER_MATVEC = 4
 # mean DRAM bytes per launch of gemv_n/gemv_h<KindDF> at the paper shape (ncu dram__bytes
 # read + write on Nm=2000, 3.238e9 and 3.212e9 B, scaled by 5 in Nm)
 GEMV_DF_TRAFFIC = 16.12e9
