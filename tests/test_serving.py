@@ -47,11 +47,11 @@ def alone(ops, r):
     return (op.matvec(r.x) if r.which == "F" else op.rmatvec(r.x)).cpu().numpy()
 
 
-@pytest.mark.parametrize("graphs", [True, False])
-def test_mix_equals_alone_and_oracle(env, graphs):
+@pytest.mark.parametrize("graphs,policy", [(True, "fifo"), (False, "fifo"), (True, "fullest")])
+def test_mix_equals_alone_and_oracle(env, graphs, policy):
     torch, ops, cols = env
     from paper_2508_10202_gb300.serve import Server
-    srv = Server(ops, budget_bytes=8 << 30, n_streams=3, graphs=graphs)
+    srv = Server(ops, budget_bytes=8 << 30, n_streams=3, graphs=graphs, policy=policy)
     reqs = make_requests(torch, ops, 40, seed=1)
     for r in reqs:
         srv.submit(r)
@@ -131,4 +131,25 @@ def test_cancel_remove_and_bad_requests(env):
             assert r.status == "done"
             np.testing.assert_allclose(r.out.cpu().numpy(), alone(ops, r), rtol=0,
                                        atol=1e-6 * float(r.out.abs().max()))
+    srv.close()
+
+
+def test_fullest_policy_order_and_starvation_guard(env):
+    # host logic only: which queued request opens the next batch
+    import time
+    torch, ops, _ = env
+    from paper_2508_10202_gb300.serve import Request, Server, ServerError
+    with pytest.raises(ServerError):
+        Server(ops, budget_bytes=8 << 30, policy="lifo")
+    srv = Server(ops, budget_bytes=8 << 30, policy="fullest", starve_ms=1e6)
+    x = {n: torch.zeros((1, op.Nt, op.Nm), device="cuda") for n, op in ops.items()}
+    first = srv.submit(Request("a", "F", x["a"]))
+    srv.submit(Request("b", "F", x["b"]))
+    srv.submit(Request("b", "F", x["b"]))
+    order = srv._order()
+    assert order[0].op == "b" and order[-1] is first      # the fuller group goes first
+    srv.starve_s = 0.0                                     # ... unless the oldest has waited too long
+    time.sleep(0.001)
+    assert srv._order()[0] is first
+    srv.run_until_idle()
     srv.close()

@@ -147,3 +147,39 @@ def test_noalloc_rejects_oversize_and_host_buffers(env):
                                  stream.cuda_stream)
     assert rc == -1 and b"device pointers" in lib.fftmv_last_error()
     op.free()
+
+
+def test_noalloc_first_call_refused_inside_capture():
+    # The first call on a device looks up the scratch array's address, which
+    # must not happen inside a stream capture: in a fresh process, a first call
+    # made while the stream is capturing returns FFTMV_ESTATE (-5) with a
+    # message, the capture stays valid, and the same call succeeds afterwards.
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = r"""
+import sys, torch
+sys.path.insert(0, %r)
+import synth
+from paper_2508_10202_gb300 import Operator, build, _lib
+build.build()
+lib = _lib.lib()
+op = Operator(torch.from_numpy(synth.block_column(16, 3, 8, seed=0)).cuda())
+m = torch.zeros((16, 8), dtype=torch.float64, device="cuda")
+y = torch.empty((16, 3), dtype=torch.float64, device="cuda")
+s = torch.cuda.Stream()
+torch.cuda.synchronize()
+g = torch.cuda.CUDAGraph()
+with torch.cuda.stream(s):
+    g.capture_begin(capture_error_mode="thread_local")
+    rc = lib.fftmv_apply_noalloc(op.handle, 0, m.data_ptr(), y.data_ptr(), 1, 0, s.cuda_stream)
+    msg = lib.fftmv_last_error().decode()
+    g.capture_end()
+rc2 = lib.fftmv_apply_noalloc(op.handle, 0, m.data_ptr(), y.data_ptr(), 1, 0, s.cuda_stream)
+torch.cuda.synchronize()
+print(rc, rc2, "before capturing" in msg)
+""" % root
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().splitlines()[-1] == "-5 0 True", r.stdout
