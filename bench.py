@@ -72,6 +72,18 @@ KERNELS_PER_MATVEC = 4
 # mean DRAM bytes per launch of gemv_n/gemv_h<KindDF> at the paper shape (ncu dram__bytes
 # read + write on Nm=2000, 3.238e9 and 3.212e9 B, scaled by 5 in Nm)
 GEMV_DF_TRAFFIC = 16.12e9
+# DRAM bytes (read + write) per K=64 bf16x2 call at the paper shape, per kernel, from
+# ncu captures at Nm=2000 (profiles/fft_L2000_Nm2000_full.md, tc_gemm_k64_Nm2000_full.md)
+# scaled by 5 in Nm where the traffic grows with Nm; the parts that do not (F*'s B planes
+# of 100 data channels, the small FFTs over Nd channels) are taken at their algorithmic size
+MULTI_RHS_DRAM = {
+    "F": {"rfft_dif (B planes)": (0.5121 + 0.9915) * 5e9,
+          "tc_gemm<0>": (1.602 + 1.1648) * 5e9 + 0.0499e9,   # A and B planes scale; D-hat out does not
+          "irfft (Nd channels)": 64 * 1001 * 100 * 8 + 64 * 1000 * 100 * 4},
+    "F*": {"rfft (Nd channels)": 64 * 1000 * 100 * 4 + 2 * 128 * 128 * 1001 * 2,
+           "tc_gemm<1>": 1.602 * 5e9 + 0.066e9 + 0.9849 * 5e9,
+           "irfft_dif": (1.0252 + 0.4812) * 5e9},
+}
 
 
 def parse_args(argv=None):
@@ -431,7 +443,7 @@ def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: in
     bf16_peak = load_tensor_peak()
     tb = a_bytes + io_bytes
     desc = ("bf16 hi+lo" if mode == "bf16x2" else "FP16 hi+lo, power-of-two scale per frequency and per RHS")
-    return {"which": which, "K": K, "prec": f"sssss/{mode} (tcgen05, {desc}, FP32 accumulate)", "ms_call": ms,
+    res = {"which": which, "K": K, "prec": f"sssss/{mode} (tcgen05, {desc}, FP32 accumulate)", "ms_call": ms,
             "matvec_s": K / (ms * 1e-3), "phase_ms": ph, "rel_err_8_rhs": err,
             "tc_kernel": {"hbm_bytes": tb, "achieved_GBs": tb / tc_s / 1e9,
                           "hbm_frac": tb / tc_s / 1e9 / hbm,
@@ -439,6 +451,12 @@ def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: in
                           "tensor_frac": flops_exec / tc_s / 1e12 / bf16_peak,
                           "useful_TFLOPs": 8.0 * Nf * Nd * Nm * K / tc_s / 1e12},
             "algorithmic_bytes_per_call": int((Nt + 1) * Nd * Nm * 8 + K * Nt * Nm * 4 + K * Nt * Nd * 4)}
+    if (Nt, Nd, Nm, K, mode) == (NT, ND, NM, 64, "bf16x2"):
+        dram = MULTI_RHS_DRAM[which]
+        res["dram_bytes_per_call"] = {"total": sum(dram.values()), "per_kernel": dram,
+                                      "vs_algorithmic": sum(dram.values()) / res["algorithmic_bytes_per_call"],
+                                      "source": "ncu dram__bytes read+write at Nm=2000, scaled to Nm=10000"}
+    return res
 
 
 def bench_small(torch, dev, calls: int = 2000) -> dict:
