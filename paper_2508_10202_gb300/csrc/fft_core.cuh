@@ -26,7 +26,9 @@
 //            48 significant bits); sums use TwoSum + Fast2Sum renormalisation,
 //            products an FMA-exact TwoProd plus the hi*lo cross terms.  The
 //            adds are the normwise-accurate ("sloppy") double-word sums, which
-//            is the accuracy an FFT's normwise error analysis needs.
+//            is the accuracy an FFT's normwise error analysis needs.  The FFT
+//            phases run it with lazy renormalisation (DFL, below): the same
+//            normwise accuracy with a quarter fewer operations.
 
 #pragma once
 
@@ -41,6 +43,7 @@ namespace fftmv {
 namespace {
 
 struct DFP {};  // precision tag: double-float on the FP32 pipe
+struct DFL {};  // the same format with lazy renormalisation (Ar<DFL>)
 
 // a real constant in every precision: FP64 value and its FP32 hi/lo split
 struct Kc {
@@ -178,6 +181,81 @@ template <> struct Ar<DFP> {
   __device__ __forceinline__ static float to_f(R x) { return __fadd_rn(x.h, x.l); }
   __device__ __forceinline__ static R zero() { return dfr{0.f, 0.f}; }
 };
+
+// Double-float with lazy renormalisation: a sum keeps TwoSum's exact error of
+// the hi parts and adds the lo parts to it (8 operations), a product keeps the
+// FMA-exact TwoProd with the cross terms (4), with no Fast2Sum at the end.  So
+// hi + lo is no longer normalised (after a cancellation lo can be several ulp
+// of hi), but it is exact to within the lo parts' own FP32 roundings, which
+// are of order u^2 times the operands' magnitudes: the normwise accuracy an
+// FFT's error analysis asks of each operation, as for DFP.  The only term a
+// product drops, lo*lo, stays below u^2 of the operands' magnitudes with an
+// unnormalised lo as well.  Stores to the FMT_DF format renormalise (TwoSum,
+// as |lo| <= |hi| no longer holds).
+__device__ __forceinline__ dfr dfl_add(dfr a, dfr b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return dfr{s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+__device__ __forceinline__ dfr dfl_mul(dfr a, dfr b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return dfr{p, e};
+}
+// a*b + sgn*c*d
+__device__ __forceinline__ dfr dfl_dot2(dfr a, dfr b, dfr c, dfr d, float sgn) {
+  const float p1 = __fmul_rn(a.h, b.h);
+  const float p2 = __fmul_rn(sgn * c.h, d.h);
+  const float e1 = __fmaf_rn(a.h, b.h, -p1);
+  const float e2 = __fmaf_rn(sgn * c.h, d.h, -p2);
+  float s, t;
+  two_sum(p1, p2, s, t);
+  t = __fadd_rn(t, __fadd_rn(e1, e2));
+  t = __fmaf_rn(a.h, b.l, t);
+  t = __fmaf_rn(a.l, b.h, t);
+  t = __fmaf_rn(sgn * c.h, d.l, t);
+  t = __fmaf_rn(sgn * c.l, d.h, t);
+  return dfr{s, t};
+}
+__device__ __forceinline__ dfr dfl_norm(dfr a) {
+  float s, e;
+  two_sum(a.h, a.l, s, e);
+  return dfr{s, e};
+}
+template <> struct Ar<DFL> {
+  using R = dfr;
+  using C = float4;
+  __device__ __forceinline__ static R add(R a, R b) { return dfl_add(a, b); }
+  __device__ __forceinline__ static R sub(R a, R b) { return dfl_add(a, df_neg(b)); }
+  __device__ __forceinline__ static R neg(R a) { return df_neg(a); }
+  __device__ __forceinline__ static R half(R a) { return dfr{0.5f * a.h, 0.5f * a.l}; }
+  __device__ __forceinline__ static R mulk(R a, const Kc& k) { return dfl_mul(a, dfr{k.h, k.l}); }
+  __device__ __forceinline__ static R re(C c) { return dfr{c.x, c.z}; }
+  __device__ __forceinline__ static R im(C c) { return dfr{c.y, c.w}; }
+  __device__ __forceinline__ static C mk(R r, R i) { return make_float4(r.h, i.h, r.l, i.l); }
+  __device__ __forceinline__ static C cmul(C a, C w) {
+    const dfr ar = re(a), ai = im(a), wr = re(w), wi = im(w);
+    return mk(dfl_dot2(ar, wr, ai, wi, -1.f), dfl_dot2(ar, wi, ai, wr, 1.f));
+  }
+  __device__ __forceinline__ static C conj(C a) { return make_float4(a.x, -a.y, a.z, -a.w); }
+  __device__ __forceinline__ static R from_d(double x) {
+    const float h = (float)x;
+    return dfr{h, (float)(x - (double)h)};
+  }
+  __device__ __forceinline__ static R from_f(float x) { return dfr{x, 0.f}; }
+  __device__ __forceinline__ static double to_d(R x) { return (double)x.h + (double)x.l; }
+  __device__ __forceinline__ static float to_f(R x) { return __fadd_rn(x.h, x.l); }
+  __device__ __forceinline__ static R zero() { return dfr{0.f, 0.f}; }
+};
+
+// the double-float arithmetic of the FFT phases: lazy renormalisation (DFL)
+// unless FFTMV_DF_LAZY=0 (DFP, every result renormalised)
+#ifndef FFTMV_DF_LAZY
+#define FFTMV_DF_LAZY 1
+#endif
+using DFA = std::conditional<FFTMV_DF_LAZY != 0, DFL, DFP>::type;
 
 // complex helpers built on the traits
 template <typename P> struct Cx {
@@ -697,6 +775,8 @@ __device__ __forceinline__ void store_cx(void* X, int64_t i, int fmt, typename A
       static_cast<float4*>(X)[i] = make_float4(hr, hm, (float)(r - (double)hr), (float)(m - (double)hm));
     } else if constexpr (std::is_same<P, DFP>::value) {
       static_cast<float4*>(X)[i] = Ar<DFP>::mk(re, im);
+    } else if constexpr (std::is_same<P, DFL>::value) {
+      static_cast<float4*>(X)[i] = Ar<DFL>::mk(dfl_norm(re), dfl_norm(im));
     } else {
       static_cast<float4*>(X)[i] = make_float4(A::to_f(re), A::to_f(im), 0.f, 0.f);
     }
@@ -716,7 +796,7 @@ __device__ __forceinline__ typename Ar<P>::C load_cx(const void* X, int64_t i, i
     return A::mk(A::from_f(v.x), A::from_f(v.y));
   }
   const float4 v = __ldg(static_cast<const float4*>(X) + i);
-  if constexpr (std::is_same<P, DFP>::value) {
+  if constexpr (std::is_same<P, DFP>::value || std::is_same<P, DFL>::value) {
     return v;
   } else if constexpr (std::is_same<P, double>::value) {
     return A::mk((double)v.x + (double)v.z, (double)v.y + (double)v.w);

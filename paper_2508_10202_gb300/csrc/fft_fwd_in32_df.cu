@@ -3,5 +3,5 @@
 #include "fft_launch.cuh"
 
 namespace fftmv {
-cudaError_t launch_rfft_fwd_float_df(const FwdDesc& d, cudaStream_t s) { return fwd_launch<float, DFP>(d, s); }
+cudaError_t launch_rfft_fwd_float_df(const FwdDesc& d, cudaStream_t s) { return fwd_launch<float, DFA>(d, s); }
 }  // namespace fftmv

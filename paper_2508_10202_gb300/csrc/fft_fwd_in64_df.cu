@@ -3,5 +3,5 @@
 #include "fft_launch.cuh"
 
 namespace fftmv {
-cudaError_t launch_rfft_fwd_double_df(const FwdDesc& d, cudaStream_t s) { return fwd_launch<double, DFP>(d, s); }
+cudaError_t launch_rfft_fwd_double_df(const FwdDesc& d, cudaStream_t s) { return fwd_launch<double, DFA>(d, s); }
 }  // namespace fftmv

@@ -3,5 +3,5 @@
 #include "fft_launch.cuh"
 
 namespace fftmv {
-cudaError_t launch_irfft_inv_df_float(const InvDesc& d, cudaStream_t s) { return inv_launch<DFP, float>(d, s); }
+cudaError_t launch_irfft_inv_df_float(const InvDesc& d, cudaStream_t s) { return inv_launch<DFA, float>(d, s); }
 }  // namespace fftmv

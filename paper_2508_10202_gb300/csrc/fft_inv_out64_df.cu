@@ -3,5 +3,5 @@
 #include "fft_launch.cuh"
 
 namespace fftmv {
-cudaError_t launch_irfft_inv_df_double(const InvDesc& d, cudaStream_t s) { return inv_launch<DFP, double>(d, s); }
+cudaError_t launch_irfft_inv_df_double(const InvDesc& d, cudaStream_t s) { return inv_launch<DFA, double>(d, s); }
 }  // namespace fftmv

@@ -1,9 +1,11 @@
 // Dispatch of the batched real FFTs: the compile-time-length kernels
-// (in-place decimation in frequency for FP32, fft_dif.cuh; Stockham for the
-// other precisions, fft_core.cuh) and the runtime-length Stockham kernels.
+// (in-place decimation in frequency for FP32, fft_dif.cuh, and for
+// double-float, fft_dif_df.cuh; Stockham for FP64 and the other lengths,
+// fft_core.cuh) and the runtime-length Stockham kernels.
 #pragma once
 
 #include "fft_dif.cuh"
+#include "fft_dif_df.cuh"
 
 namespace fftmv {
 namespace {
@@ -13,6 +15,10 @@ namespace {
 #endif
 // the lengths with in-place decimation-in-frequency FP32 kernels (dif_plan)
 #define FFTMV_DIF_LENGTHS(X) X(128) X(256) X(512) X(1000) X(2000)
+// ... and double-float ones (dfd_plan, fft_dif_df.cuh)
+#ifndef FFTMV_DFD
+#define FFTMV_DFD 1
+#endif
 
 template <typename Tin, typename P>
 cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
@@ -32,6 +38,12 @@ cudaError_t fwd_launch(const FwdDesc& d, cudaStream_t s) {
         default: break;
       }
     }
+  }
+#endif
+#if FFTMV_DFD
+  if constexpr (std::is_same<P, DFA>::value) {
+    cudaError_t e;
+    if (fwd_dfd_try<Tin>(d, np, s, e)) return e;
   }
 #endif
   if (np == fft_pairs<P>(d.plan.L)) {
@@ -65,6 +77,12 @@ cudaError_t inv_launch(const InvDesc& d, cudaStream_t s) {
         default: break;
       }
     }
+  }
+#endif
+#if FFTMV_DFD
+  if constexpr (std::is_same<P, DFA>::value) {
+    cudaError_t e;
+    if (inv_dfd_try<Tout>(d, np, s, e)) return e;
   }
 #endif
   if (np == fft_pairs<P>(d.plan.L)) {

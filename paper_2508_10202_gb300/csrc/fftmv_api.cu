@@ -121,6 +121,7 @@ struct fftmv_op {
   float2* tw32 = nullptr;
   float4* twdf = nullptr;     // twiddles as FP32 hi/lo pairs
   float2* twdif32 = nullptr;  // twiddle table of the length's DifPlan (FP32), when it has one
+  float4* twdfd = nullptr;    // twiddle table of the length's dfd_plan (double-float), when it has one
   double2* fhat64 = nullptr;  // master F-hat [Nf][Nd][ldn], FP64
   float4* fhat_df = nullptr;  // FP32 hi/lo pairs
   float2* fhat32 = nullptr;   // FP32
@@ -199,6 +200,7 @@ void release(fftmv_op* op) {
   cudaFree(op->tw32);
   cudaFree(op->twdf);
   cudaFree(op->twdif32);
+  cudaFree(op->twdfd);
   cudaFree(op->fhat64);
   cudaFree(op->fhat_df);
   cudaFree(op->fhat32);
@@ -293,6 +295,7 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   f.fmt = c.in_fmt;
   f.pad_single = p.pad == FFTMV_F32;
   f.twd = fprec == FFT_F32 ? op->twdif32 : nullptr;
+  f.twdd = fprec == FFT_DF ? op->twdfd : nullptr;
   {
     const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
     f.pair_ok = (reinterpret_cast<uintptr_t>(x) % (2 * esz) == 0) && f.x_ld_t % 2 == 0 && f.x_ld_b % 2 == 0;
@@ -381,6 +384,7 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
     v.inv_L_hi = (float)v.inv_L;
     v.inv_L_lo = (float)(v.inv_L - (double)v.inv_L_hi);
     v.twd = iprec == FFT_F32 ? op->twdif32 : nullptr;
+    v.twdd = iprec == FFT_DF ? op->twdfd : nullptr;
     {
       const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;
       v.out_pair_ok = reinterpret_cast<uintptr_t>(y) % (2 * esz) == 0 && v.y_ld_t % 2 == 0 && v.y_ld_b % 2 == 0;
@@ -590,6 +594,29 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
     }
     if ((rc = cu(cudaMalloc(&op->twdif32, twd.size() * sizeof(float2)), "cudaMalloc(twiddles)"))) return rc;
     if ((rc = cu(cudaMemcpy(op->twdif32, twd.data(), twd.size() * sizeof(float2), cudaMemcpyHostToDevice),
+                 "twiddle copy")))
+      return rc;
+  }
+
+  if (dfd_plan((int)L).n > 0) {
+    // the same rows for the double-float plan, each entry hi/lo pairs of the
+    // long double value
+    const DifPlan pl = dfd_plan((int)L);
+    std::vector<float4> twd((size_t)dfd_tw_size((int)L));
+    for (int sp = 0; sp < pl.n; ++sp) {
+      const int M = dfd_M((int)L, sp), S = dfd_S((int)L, sp), R = pl.rad[sp];
+      if (S == 1) continue;
+      for (int j = 0; j < S; ++j)
+        for (int q = 1; q < R; ++q) {
+          const long double a = -2.0L * 3.141592653589793238462643383279502884L * (long double)(j * q) / (long double)M;
+          const long double c = cosl(a), sn = sinl(a);
+          const float ch = (float)c, sh = (float)sn;
+          twd[(size_t)dfd_tw_offset((int)L, sp) + (size_t)j * (R - 1) + (q - 1)] =
+              make_float4(ch, sh, (float)(c - (long double)ch), (float)(sn - (long double)sh));
+        }
+    }
+    if ((rc = cu(cudaMalloc(&op->twdfd, twd.size() * sizeof(float4)), "cudaMalloc(twiddles)"))) return rc;
+    if ((rc = cu(cudaMemcpy(op->twdfd, twd.data(), twd.size() * sizeof(float4), cudaMemcpyHostToDevice),
                  "twiddle copy")))
       return rc;
   }

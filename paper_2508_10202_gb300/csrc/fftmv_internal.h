@@ -55,7 +55,7 @@ struct FftPlan {
 // position r_0 S_0 + r_1 S_1 + r_2 S_2 ...
 struct DifPlan {
   int n;
-  int rad[4];
+  int rad[5];
 };
 __host__ __device__ constexpr DifPlan dif_plan(int L) {
   return L == 2000 ? DifPlan{3, {16, 5, 25, 1}}
@@ -83,6 +83,28 @@ __host__ __device__ constexpr int dif_tw_offset(int L, int s) {
 }
 __host__ __device__ constexpr int dif_tw_size(int L) { return dif_tw_offset(L, dif_plan(L).n); }
 
+// Plans of the double-float in-place kernels (fft_dif_df.cuh), with the same
+// conventions.  A double-float complex takes four registers, so the radices
+// stay at 8 and below: 2000 = 8 2 5 5 5, 1000 = 8 5 5 5.  Their twiddle table
+// has S_s rows of rad[s] - 1 entries for every pass with S_s > 1, each entry a
+// double-float complex in the FMT_DF layout (re_hi, im_hi, re_lo, im_lo).
+__host__ __device__ constexpr DifPlan dfd_plan(int L) {
+  return L == 2000 ? DifPlan{5, {8, 2, 5, 5, 5}} : L == 1000 ? DifPlan{4, {8, 5, 5, 5, 1}} : DifPlan{0, {1, 1, 1, 1, 1}};
+}
+__host__ __device__ constexpr int dfd_M(int L, int s) {
+  int m = L;
+  for (int i = 0; i < s; ++i) m /= dfd_plan(L).rad[i];
+  return m;
+}
+__host__ __device__ constexpr int dfd_S(int L, int s) { return dfd_M(L, s) / dfd_plan(L).rad[s]; }
+__host__ __device__ constexpr int dfd_tw_offset(int L, int s) {
+  int off = 0;
+  for (int i = 0; i < s; ++i)
+    if (dfd_S(L, i) > 1) off += dfd_S(L, i) * (dfd_plan(L).rad[i] - 1);
+  return off;
+}
+__host__ __device__ constexpr int dfd_tw_size(int L) { return dfd_tw_offset(L, dfd_plan(L).n); }
+
 // Forward real FFT of zero-padded channels (phases 1-2 fused).
 // Channel c = (row, col) with col < cols; channels (2q, 2q+1) of a row are
 // transformed together as one complex signal.  x[b][t][row][col] is read for
@@ -109,6 +131,7 @@ struct FwdDesc {
   // power of two 2^e_b, e_b = range_exp(in_absmax[b]), as it loads it.
   const unsigned long long* in_absmax;
   const void* twd;         // twiddle table of the length's DifPlan (FP32 complexes), or null
+  const void* twdd;        // twiddle table of the length's dfd_plan (double-float complexes), or null
 };
 
 // Inverse real FFT of Hermitian half spectra followed by unpad (phases 4-5 fused).
@@ -135,6 +158,7 @@ struct InvDesc {
   const unsigned long long* rhs_absmax;
   int mid_exp, out_exp;
   const void* twd;         // twiddle table of the length's DifPlan (FP32 complexes), or null
+  const void* twdd;        // twiddle table of the length's dfd_plan (double-float complexes), or null
   int out_pair_ok;         // y and its strides allow storing channels (c, c+1) as one vector
 };
 
