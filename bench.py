@@ -462,8 +462,9 @@ def bench_multi_rhs(torch, op, Fcol, dev, stream, peaks, which: str = "F", K: in
 def bench_small(torch, dev, calls: int = 2000) -> dict:
     """The plain FP64 workload Nt=64, Nd=8, Nm=32 (F-hat 266 KB, resident in L2):
     latency-bound, so it reports microseconds per call, issued directly and as
-    a replayed CUDA graph of caller-scratch calls; a roofline fraction means
-    nothing at this size."""
+    a replayed CUDA graph of caller-scratch calls, for the fused single-launch
+    path (one 16-CTA cluster per call, the default at this size) and for the
+    three-kernel path; a roofline fraction means nothing at this size."""
     import synth
     from paper_2508_10202_gb300 import Operator
     Nt, Nd, Nm = 64, 8, 32
@@ -489,29 +490,37 @@ def bench_small(torch, dev, calls: int = 2000) -> dict:
     def direct():
         op.matvec(m, out=y, stream=s)
         op.rmatvec(d, out=x, stream=s)
-    us_direct = timed(direct)
-    wf, wa = op.workspace_bytes("F", 1), op.workspace_bytes("F*", 1)
-    ws = torch.empty(max(wf, wa) + 256, dtype=torch.uint8, device=dev)
-    off = (-ws.data_ptr()) % 256
-    wsf = ws[off:off + wf]
-    wsa = ws[off:off + wa]
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(s):
-        op.apply_ws("F", m, y, wsf, stream=s)
-        op.apply_ws("F*", d, x, wsa, stream=s)
-    torch.cuda.synchronize(dev)
-    with torch.cuda.graph(g, stream=s):
-        op.apply_ws("F", m, y, wsf, stream=s)
-        op.apply_ws("F*", d, x, wsa, stream=s)
 
-    def graphed():
+    def run() -> tuple[float, float]:
+        us_direct = timed(direct)
+        wf, wa = op.workspace_bytes("F", 1), op.workspace_bytes("F*", 1)
+        ws = torch.empty(max(wf, wa) + 256, dtype=torch.uint8, device=dev)
+        off = (-ws.data_ptr()) % 256
+        wsf = ws[off:off + wf]
+        wsa = ws[off:off + wa]
+        g = torch.cuda.CUDAGraph()
         with torch.cuda.stream(s):
-            g.replay()
-    us_graph = timed(graphed)
+            op.apply_ws("F", m, y, wsf, stream=s)
+            op.apply_ws("F*", d, x, wsa, stream=s)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.graph(g, stream=s):
+            op.apply_ws("F", m, y, wsf, stream=s)
+            op.apply_ws("F*", d, x, wsa, stream=s)
+
+        def graphed():
+            with torch.cuda.stream(s):
+                g.replay()
+        return us_direct, timed(graphed)
+
+    us_direct, us_graph = run()
+    op.set_fusion(False)
+    us_direct3, us_graph3 = run()
     op.free()
     return {"workload": "plain FP64, Nt=64 Nd=8 Nm=32, F and F* alternating", "precision": "ddddd/native",
             "us_per_matvec_direct": us_direct, "us_per_matvec_graph": us_graph,
-            "matvec_s_graph": 1e6 / us_graph, "roofline": "not meaningful: launch- and latency-bound"}
+            "matvec_s_graph": 1e6 / us_graph, "path": "fused: one cluster launch per call",
+            "three_kernel_path": {"us_per_matvec_direct": us_direct3, "us_per_matvec_graph": us_graph3},
+            "roofline": "not meaningful: launch- and latency-bound"}
 
 
 def bench_hessian(torch, op, Fcol, stream, batch: int = 64, batches: int = 4) -> dict:

@@ -168,13 +168,27 @@ int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out)
  * Errors: EINVAL / ESTATE for a bad handle. */
 int fftmv_set_scratch_limit(fftmv_op* op, size_t bytes);
 
+/* Fused small-operator calls (Section 2.4's five phases in one launch; on by
+ * default).  A call whose precision is all FP64 with native arithmetic
+ * (pad, FFT, GEMV, IFFT, unpad = F64; gemv_mode = fft_mode = NATIVE), whose FFT
+ * length L is 128 or 256 and whose input and output channel counts are both
+ * at most 64 runs as one launch per call: one cluster of 8 CTAs per right-hand
+ * side keeps both spectra in shared memory (exchanged through distributed
+ * shared memory) and takes no scratch from the pool.  Its results equal the
+ * three-kernel path's up to the rounding order of the FP64 sums; with timing
+ * on, its whole duration is reported as the first phase.  enable = 0 sends
+ * every call through the three-kernel path.  Errors: EINVAL / ESTATE for a bad
+ * handle. */
+int fftmv_set_fusion(fftmv_op* op, int enable);
+
 /* F m (which = FFTMV_FORWARD) or F* d (FFTMV_ADJOINT) with caller-supplied
  * scratch, so a serving layer can own and account for every byte and capture
  * the call in a CUDA graph (no allocation happens inside).
  *   in, out   : device pointers (host buffers: FFTMV_EINVAL).
  *   workspace : device memory, 256-byte aligned, at least
  *               fftmv_workspace_bytes(op, which, K) bytes; used only by this
- *               call until the stream has run it.
+ *               call until the stream has run it.  May be null when that size
+ *               is 0 (a fused call, fftmv_set_fusion).
  * Everything else as fftmv_matvec / fftmv_rmatvec. */
 int fftmv_apply_ws(fftmv_op* op, int which, const void* in, void* out, int64_t K, int io_dtype, void* workspace,
                    size_t workspace_bytes, void* stream);

@@ -138,6 +138,7 @@ struct fftmv_op {
   int64_t calls[2] = {};
   size_t scratch_limit = 0;  // 0: kCallScratchBudget
   int fexp = 0;              // range exponent of F-hat: max |Re, Im| / 2^fexp in [1, 2)
+  bool fusion = true;        // small all-FP64 calls as one fused launch (fftmv_set_fusion)
 };
 
 namespace {
@@ -238,7 +239,17 @@ struct CallPlan {
   size_t in_hat, out_hat;  // bytes
   bool scaled;             // range scaling: K absmax words at in_hat + absmax_off
   size_t absmax_off;
+  bool fused;              // one fused launch (fused_small.cu), no spectra in scratch
 };
+
+// all five phases in native FP64 on an operator whose spectra fit one cluster
+bool fused_call(const fftmv_op* op, int which) {
+  const fftmv_precision& p = op->prec[which];
+  const bool fwd = which == FFTMV_FORWARD;
+  return op->fusion && p.pad == FFTMV_F64 && p.fft == FFTMV_F64 && p.gemv == FFTMV_F64 && p.ifft == FFTMV_F64 &&
+         p.unpad == FFTMV_F64 && p.gemv_mode == FFTMV_GEMV_NATIVE && p.fft_mode == FFTMV_GEMV_NATIVE &&
+         fused_small_fits(op->L, fwd ? op->Nm : op->Nd, fwd ? op->Nd : op->Nm);
+}
 
 CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
   CallPlan c{};
@@ -264,6 +275,8 @@ CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
     c.in_hat += align256((size_t)K * sizeof(unsigned long long));
   }
   c.out_hat = align256((size_t)K * op->Nf * c.out_ld * fmt_bytes(c.out_fmt));
+  c.fused = fused_call(op, which) && K <= 65535;
+  if (c.fused) c.in_hat = c.out_hat = 0;
   return c;
 }
 
@@ -276,6 +289,32 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   const int fprec = fft_prec(p.fft, p.fft_mode), iprec = fft_prec(p.ifft, p.fft_mode);
   const bool fwd = which == FFTMV_FORWARD;
   if (ev) cudaEventRecord(ev[0], s);
+  if (c.fused) {   // the whole call is one launch; its time is reported as the first phase
+    FusedDesc u{};
+    u.x = x;
+    u.y = y;
+    u.F = op->fhat64;
+    u.tw = op->tw64;
+    u.Nt = (int)op->Nt;
+    u.L = (int)op->L;
+    u.Nd = (int)op->Nd;
+    u.ldn = (int)op->ldn;
+    u.Cin = (int)c.Cin;
+    u.Cout = (int)c.Cout;
+    u.K = (int)K;
+    u.adjoint = !fwd;
+    u.io_f32 = io == FFTMV_IO_F32;
+    u.x_ld_b = op->Nt * c.Cin;
+    u.y_ld_b = op->Nt * c.Cout;
+    u.inv_L = 1.0 / (double)op->L;
+    const cudaError_t e = launch_fused_small(u, s);
+    if (ev) {
+      cudaEventRecord(ev[1], s);
+      cudaEventRecord(ev[2], s);
+      cudaEventRecord(ev[3], s);
+    }
+    return e;
+  }
   FwdDesc f{};
   f.plan = op->plan;
   f.tw = fprec == FFT_F32 ? (const void*)op->tw32 : fprec == FFT_DF ? (const void*)op->twdf : (const void*)op->tw64;
@@ -437,8 +476,8 @@ int run_chunk(fftmv_op* op, int which, const void* in, void* out, int64_t K, int
   const size_t stage_out = out_dev ? 0 : align256(out_bytes);
   const size_t total = c.in_hat + c.out_hat + stage_in + stage_out;
 
-  char* ws = nullptr;
-  CUDA_TRY(cudaMallocFromPoolAsync((void**)&ws, total, op->pool, s));
+  char* ws = nullptr;   // none for a fused call on device buffers
+  if (total > 0) CUDA_TRY(cudaMallocFromPoolAsync((void**)&ws, total, op->pool, s));
   char* in_hat = ws;
   char* out_hat = ws + c.in_hat;
   const void* x = in;
@@ -447,7 +486,7 @@ int run_chunk(fftmv_op* op, int which, const void* in, void* out, int64_t K, int
     void* st = out_hat + c.out_hat;
     cudaError_t e = cudaMemcpyAsync(st, in, in_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
-      cudaFreeAsync(ws, s);
+      if (ws) cudaFreeAsync(ws, s);
       return cuda_fail(e, "cudaMemcpyAsync(host input)");
     }
     x = st;
@@ -476,7 +515,7 @@ int run_chunk(fftmv_op* op, int which, const void* in, void* out, int64_t K, int
     op->pending.push_back(ts);
   }
   if (e == cudaSuccess && !out_dev) e = cudaMemcpyAsync(out, y, out_bytes, cudaMemcpyDeviceToHost, s);
-  cudaError_t ef = cudaFreeAsync(ws, s);
+  cudaError_t ef = ws ? cudaFreeAsync(ws, s) : cudaSuccess;
   if (e != cudaSuccess) return cuda_fail(e, "matvec kernels");
   if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
   return FFTMV_OK;
@@ -760,6 +799,12 @@ int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out)
   return FFTMV_OK;
 }
 
+int fftmv_set_fusion(fftmv_op* op, int enable) {
+  if (int rc = check_op(op)) return rc;
+  op->fusion = enable != 0;
+  return FFTMV_OK;
+}
+
 int fftmv_set_scratch_limit(fftmv_op* op, size_t bytes) {
   int rc = check_op(op);
   if (rc) return rc;
@@ -775,11 +820,12 @@ int fftmv_apply_ws(fftmv_op* op, int which, const void* in, void* out, int64_t K
   if (K < 0) return fail(FFTMV_EINVAL, "K = %lld < 0", (long long)K);
   if (io != FFTMV_IO_F64 && io != FFTMV_IO_F32) return fail(FFTMV_EINVAL, "io_dtype %d unknown", io);
   if (K == 0) return FFTMV_OK;
-  if (!in || !out || !workspace) return fail(FFTMV_EINVAL, "null input, output or workspace");
+  if (!in || !out) return fail(FFTMV_EINVAL, "null input or output");
   if (K > 65535) return fail(FFTMV_EUNSUPPORTED, "K = %lld exceeds 65535 right-hand sides per call", (long long)K);
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(FFTMV_EINVAL, "workspace is not 256-byte aligned");
   DeviceGuard dg(op->device);
   const CallPlan c = plan_call(op, which, K);
+  if (!workspace && c.in_hat + c.out_hat > 0) return fail(FFTMV_EINVAL, "null workspace");
   if (workspace_bytes < c.in_hat + c.out_hat)
     return fail(FFTMV_EINVAL, "workspace of %zu bytes; this call needs %zu", workspace_bytes, c.in_hat + c.out_hat);
   const size_t esz = io == FFTMV_IO_F32 ? 4 : 8;

@@ -150,6 +150,10 @@ class Operator:
         L.check(L.lib().fftmv_workspace_bytes(self.handle, _WHICH[which], K, ctypes.byref(out)))
         return out.value
 
+    def set_fusion(self, enable: bool = True) -> None:
+        """Small all-FP64 calls as one fused launch (fftmv_set_fusion; on by default)."""
+        L.check(L.lib().fftmv_set_fusion(self.handle, int(bool(enable))))
+
     def set_scratch_limit(self, nbytes: int = 0) -> None:
         """Bound the pool scratch of one launch sequence; larger K runs in chunks (0: 8 GiB)."""
         L.check(L.lib().fftmv_set_scratch_limit(self.handle, int(nbytes)))
