@@ -29,6 +29,9 @@ namespace fftmv {
 namespace {
 
 constexpr int kDifPad = 2;
+#ifndef FFTMV_DIF_HALF
+#define FFTMV_DIF_HALF 1
+#endif
 #ifndef FFTMV_DIF_UNROLL
 #define FFTMV_DIF_UNROLL 1
 #endif
@@ -397,7 +400,9 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
 
 // Inverse: Hermitian assembly + inverse complex FFT + unpad; grid (channel
 // group, K), as irfft_inv_kernel.  The last pass writes t < Nt straight to HBM.
-template <typename Tout, int NP, int L>
+// HALF: Nt = L / 2, so which of the final pass's outputs fall in t < Nt is
+// known at compile time (all of the first R/2, none past it but one)
+template <typename Tout, int NP, int L, bool HALF>
 __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>()) irfft_dif_kernel(InvDesc d) {
   using P = float;
   using A = Ar<P>;
@@ -496,7 +501,14 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
     const bool two = c + 1 < d.cols;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      if (tb + (L / R) * q >= Nt) continue;
+      if constexpr (HALF) {
+        // t = tb + (L/R) q with 0 <= tb < L/R: always below L/2 for
+        // (q + 1) (L/R) <= L/2, never for q (L/R) >= L/2
+        if ((q * (L / R)) >= L / 2) continue;
+        if ((q + 1) * (L / R) > L / 2 && tb + (L / R) * q >= L / 2) continue;
+      } else {
+        if (tb + (L / R) * q >= Nt) continue;
+      }
       Tout* yq = yb + q * ystep;
       const float re = v[q].x * invL, im = v[q].y * invL;
       if (vec && two) {
@@ -527,14 +539,21 @@ cudaError_t fwd_dif_launch(const FwdDesc& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename Tout, int NP, int L>
-cudaError_t inv_dif_launch(const InvDesc& d, cudaStream_t s) {
+template <typename Tout, int NP, int L, bool HALF>
+cudaError_t inv_dif_launch_h(const InvDesc& d, cudaStream_t s) {
   dim3 grid((d.cols + 2 * NP - 1) / (2 * NP), d.K);
   constexpr size_t smem = (size_t)dif_smem_elems<L, NP>() * sizeof(float2);
-  cudaError_t e = prep(irfft_dif_kernel<Tout, NP, L>, smem);
+  cudaError_t e = prep(irfft_dif_kernel<Tout, NP, L, HALF>, smem);
   if (e != cudaSuccess) return e;
-  irfft_dif_kernel<Tout, NP, L><<<grid, dif_threads<L, NP>(), smem, s>>>(d);
+  irfft_dif_kernel<Tout, NP, L, HALF><<<grid, dif_threads<L, NP>(), smem, s>>>(d);
   return cudaGetLastError();
+}
+template <typename Tout, int NP, int L>
+cudaError_t inv_dif_launch(const InvDesc& d, cudaStream_t s) {
+#if FFTMV_DIF_HALF
+  if (2 * d.Nt == L) return inv_dif_launch_h<Tout, NP, L, true>(d, s);
+#endif
+  return inv_dif_launch_h<Tout, NP, L, false>(d, s);
 }
 
 }  // namespace

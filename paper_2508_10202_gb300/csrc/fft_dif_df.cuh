@@ -26,6 +26,9 @@ namespace {
 
 // the arithmetic: DFA, double-float with lazy renormalisation (fft_core.cuh)
 using DfdP = DFA;
+#ifndef FFTMV_DIF_HALF
+#define FFTMV_DIF_HALF 1
+#endif
 
 template <int L, int NP>
 __device__ __forceinline__ int dfd_e(int pos, int p) {
@@ -204,7 +207,9 @@ __global__ void __launch_bounds__(dfd_threads<L, NP>(), FFTMV_DFD_MINB) rfft_dfd
 // Inverse: Hermitian assembly + inverse complex FFT + unpad; grid (channel
 // group, K), as irfft_inv_kernel.  The last pass writes t < Nt straight to HBM
 // (1/L scale, range scaling, unpad and output cast fused).
-template <typename Tout, int NP, int L>
+// HALF: Nt = L / 2, so which of the final pass's outputs fall in t < Nt is
+// known at compile time
+template <typename Tout, int NP, int L, bool HALF>
 __global__ void __launch_bounds__(dfd_threads<L, NP>(), FFTMV_DFD_MINB) irfft_dfd_kernel(InvDesc d) {
   using P = DfdP;
   using A = Ar<P>;
@@ -301,7 +306,12 @@ __global__ void __launch_bounds__(dfd_threads<L, NP>(), FFTMV_DFD_MINB) irfft_df
       const int64_t o0 = b * d.y_ld_b + (int64_t)tb * d.y_ld_t + c;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        if (tb + (L / R) * q >= d.Nt) continue;
+        if constexpr (HALF) {
+          if ((q * (L / R)) >= L / 2) continue;
+          if ((q + 1) * (L / R) > L / 2 && tb + (L / R) * q >= L / 2) continue;
+        } else {
+          if (tb + (L / R) * q >= d.Nt) continue;
+        }
         const int64_t o = o0 + (int64_t)q * (L / R) * d.y_ld_t;
         if constexpr (SC) {
           store_real_scaled<Tout, P>(d.y, o, A::mulk(A::re(v[q]), inv_L), d.unpad_single, s1, s2);
@@ -341,15 +351,22 @@ cudaError_t fwd_dfd_launch(const FwdDesc& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename Tout, int L>
-cudaError_t inv_dfd_launch(const InvDesc& d, cudaStream_t s) {
+template <typename Tout, int L, bool HALF>
+cudaError_t inv_dfd_launch_h(const InvDesc& d, cudaStream_t s) {
   constexpr int NP = fft_pairs<DfdP>(L);
   dim3 grid((d.cols + 2 * NP - 1) / (2 * NP), d.K);
   constexpr size_t smem = (size_t)dfd_smem_elems<L, NP>() * sizeof(float4);
-  cudaError_t e = prep(irfft_dfd_kernel<Tout, NP, L>, smem);
+  cudaError_t e = prep(irfft_dfd_kernel<Tout, NP, L, HALF>, smem);
   if (e != cudaSuccess) return e;
-  irfft_dfd_kernel<Tout, NP, L><<<grid, dfd_threads<L, NP>(), smem, s>>>(d);
+  irfft_dfd_kernel<Tout, NP, L, HALF><<<grid, dfd_threads<L, NP>(), smem, s>>>(d);
   return cudaGetLastError();
+}
+template <typename Tout, int L>
+cudaError_t inv_dfd_launch(const InvDesc& d, cudaStream_t s) {
+#if FFTMV_DIF_HALF
+  if (2 * d.Nt == L) return inv_dfd_launch_h<Tout, L, true>(d, s);
+#endif
+  return inv_dfd_launch_h<Tout, L, false>(d, s);
 }
 
 // launch the double-float in-place kernel when it applies; false: it does not
