@@ -424,9 +424,11 @@ __global__ void __launch_bounds__(dif_threads<L, NP>(), dif_min_blocks<L, NP>())
   const double midf = midsc ? ldexp(1.0, d.mid_exp) : 1.0;
   // every channel of the CTA present in FP32 pairs: one 16-byte load per
   // item and no per-item checks but the end of the spectrum
-  // (two variants that issue the pair loads without the per-item branches,
-  // checks hoisted out or indices clamped, were slower: 2.70 against 2.48 ms
-  // at K = 64)
+  // (variants that issue the pair loads without the per-item branches were
+  // slower at K = 64: checks hoisted out or indices clamped, 2.70 against
+  // 2.48 ms; every address and position a compile-time offset from the
+  // thread's own, with the edge items found at compile time, 2.53 against
+  // 2.44 ms)
   for (int i0 = threadIdx.x; i0 < Nf * NP; i0 += U * T) {
     C a[U], bb[U];
 #pragma unroll
