@@ -58,6 +58,8 @@ __global__ void __launch_bounds__(kFusedThreads) fused_small_kernel(FusedDesc d)
   constexpr int NCH = 2 * NP;         // channels per CTA
   constexpr int MAXC = NCH * CL;      // channels per cluster
   constexpr int NWL = (Nf + CL - 1) / CL;
+  // the Stockham passes give each thread ceil(E / R) butterflies of radix R <= E
+  static_assert(T * E >= L * NP, "too few threads for one pass over the CTA's signals");
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int b = blockIdx.y;
