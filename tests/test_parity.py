@@ -83,11 +83,13 @@ def test_fp64_range(torch_cuda, Nt, Nd, Nm, fexp, xexp, mode, fft_mode):
     op.free()
 
 
+@pytest.mark.parametrize("Nt,Nd,Nm", [(64, 8, 32), (1000, 4, 9)])
 @pytest.mark.parametrize("fexp,xexp", [(110, -100), (-110, 100), (-100, -20)])
-def test_fp64_class_range_fp32_io(torch_cuda, fexp, xexp):
-    # FP32 inputs and outputs (in FP32 range), an operator far outside it
+def test_fp64_class_range_fp32_io(torch_cuda, Nt, Nd, Nm, fexp, xexp):
+    # FP32 inputs and outputs (in FP32 range), an operator far outside it;
+    # Nt = 1000 runs the in-place double-float FFTs
     torch = torch_cuda
-    Fcol, m, d = make_case(64, 8, 32, K=2, seed=6)
+    Fcol, m, d = make_case(Nt, Nd, Nm, K=2, seed=6)
     Fcol = np.ldexp(Fcol, fexp)
     m32, d32 = np.ldexp(m, xexp).astype(np.float32), np.ldexp(d, xexp).astype(np.float32)
     op = gpu_op(torch, Fcol)
