@@ -135,6 +135,20 @@ typedef struct {
 int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t Nm, void* stream,
                           fftmv_op** out);
 
+/* Checkpoint of an operator (no counterpart in the paper, which keeps only
+ * output vectors): the master F-hat, [Nf][Nd][ldn] complex FP64 (re, im
+ * interleaved; row length ldn = Nm rounded up to 8, padding columns zero), the
+ * only state the setup FFT builds.  fftmv_get_fhat copies it to dst (host or
+ * device, at least Nf*Nd*ldn*16 bytes; stream ordered, synchronous for a
+ * pageable host dst).  fftmv_create_from_fhat builds an operator from such a
+ * copy instead of the block column, skipping the setup FFT: fhat is host or
+ * device memory read during the call (its padding columns are ignored and
+ * stored as zeros), Nt, Nd, Nm as for fftmv_create_operator, and the result
+ * equals the original operator's bit for bit.  Errors: EINVAL for null
+ * pointers, bad sizes or a short dst; ECUDA for a failed copy. */
+int fftmv_get_fhat(const fftmv_op* op, void* dst, size_t bytes, void* stream);
+int fftmv_create_from_fhat(const void* fhat, int64_t Nt, int64_t Nd, int64_t Nm, void* stream, fftmv_op** out);
+
 /* Set the per-phase precisions used by later calls for F (which=FORWARD) or
  * F* (which=ADJOINT) (Section 3.2: set at creation, changeable at runtime).
  * Builds the stored F-hat form the GEMV phase needs if it does not exist yet

@@ -53,6 +53,8 @@ SIGNATURES = {
     "fftmv_workspace_bytes": (_INT, [_P, _INT, _I64, ctypes.POINTER(ctypes.c_size_t)]),
     "fftmv_set_scratch_limit": (_INT, [_P, ctypes.c_size_t]),
     "fftmv_set_fusion": (_INT, [_P, ctypes.c_int]),
+    "fftmv_get_fhat": (_INT, [_P, _P, ctypes.c_size_t, _P]),
+    "fftmv_create_from_fhat": (_INT, [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, ctypes.POINTER(_P)]),
     "fftmv_apply_ws": (_INT, [_P, _INT, _P, _P, _I64, _INT, _P, ctypes.c_size_t, _P]),
     "fftmv_get_info": (_INT, [_P, ctypes.POINTER(Info)]),
     "fftmv_device_status": (_INT, [_P, ctypes.POINTER(ctypes.c_uint32), _INT]),

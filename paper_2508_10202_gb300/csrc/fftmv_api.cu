@@ -562,10 +562,16 @@ int fftmv_version(void) { return 100; }
 
 const char* fftmv_last_error(void) { return g_err.c_str(); }
 
-int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t Nm, void* stream, fftmv_op** out) {
+}  // extern "C"
+
+namespace {
+// The operator from its block column (F_col) or from a saved master F-hat
+// (fhat, [Nf][Nd][ldn] FP64 complex); exactly one of the two is given.
+int create_impl(const double* F_col, const void* fhat, int64_t Nt, int64_t Nd, int64_t Nm, void* stream,
+                fftmv_op** out) {
   if (!out) return fail(FFTMV_EINVAL, "null output handle");
   *out = nullptr;
-  if (!F_col) return fail(FFTMV_EINVAL, "null block column");
+  if (!F_col && !fhat) return fail(FFTMV_EINVAL, "null block column");
   if (Nt < 1 || Nd < 1 || Nm < 1) return fail(FFTMV_EINVAL, "sizes must be >= 1 (Nt=%lld Nd=%lld Nm=%lld)",
                                               (long long)Nt, (long long)Nd, (long long)Nm);
   const int64_t L = choose_length(Nt);
@@ -680,7 +686,14 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
   f.X_ld_b = 0;
   f.fmt = FMT_C128;
   f.pad_single = 0;
-  if (is_device_ptr(F_col)) {
+  if (fhat) {
+    // a saved spectrum: copied as it is, its padding columns n >= Nm zeroed
+    cudaError_t e = cudaMemcpyAsync(op->fhat64, fhat, fh_elems * sizeof(double2), cudaMemcpyDefault, s);
+    if (e == cudaSuccess && ldn > Nm)
+      e = cudaMemset2DAsync(op->fhat64 + Nm, ldn * sizeof(double2), 0, (ldn - Nm) * sizeof(double2), Nf * Nd, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if ((rc = cu(e, "F-hat copy"))) return rc;
+  } else if (is_device_ptr(F_col)) {
     f.x = F_col;
     f.X = op->fhat64;
     f.rows = (int)Nd;
@@ -739,6 +752,38 @@ int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t N
     g_live.insert(op);
   }
   *out = op;
+  return FFTMV_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int fftmv_create_operator(const double* F_col, int64_t Nt, int64_t Nd, int64_t Nm, void* stream, fftmv_op** out) {
+  if (!F_col) {
+    if (out) *out = nullptr;
+    return fail(FFTMV_EINVAL, "null block column");
+  }
+  return create_impl(F_col, nullptr, Nt, Nd, Nm, stream, out);
+}
+
+int fftmv_create_from_fhat(const void* fhat, int64_t Nt, int64_t Nd, int64_t Nm, void* stream, fftmv_op** out) {
+  if (!fhat) {
+    if (out) *out = nullptr;
+    return fail(FFTMV_EINVAL, "null F-hat");
+  }
+  return create_impl(nullptr, fhat, Nt, Nd, Nm, stream, out);
+}
+
+int fftmv_get_fhat(const fftmv_op* op, void* dst, size_t bytes, void* stream) {
+  int rc = check_op(op);
+  if (rc) return rc;
+  if (!dst) return fail(FFTMV_EINVAL, "null destination");
+  const size_t need = (size_t)op->Nf * op->Nd * op->ldn * sizeof(double2);
+  if (bytes < need) return fail(FFTMV_EINVAL, "destination of %zu bytes; F-hat takes %zu", bytes, need);
+  DeviceGuard dg(op->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaMemcpyAsync(dst, op->fhat64, need, cudaMemcpyDefault, s));
+  if (!is_device_ptr(dst) && !is_pinned_host(dst)) CUDA_TRY(cudaStreamSynchronize(s));
   return FFTMV_OK;
 }
 

@@ -80,6 +80,40 @@ def _stream_handle(stream, device) -> int:
     return stream.cuda_stream
 
 
+FHAT_HEADER_BYTES = 4096
+_FHAT_FORMAT = "fftmv-fhat"
+
+
+def fhat_header(Nt: int, Nd: int, Nm: int, L_: int, ldn: int) -> bytes:
+    """The header block of a saved F-hat: JSON, space padded to FHAT_HEADER_BYTES."""
+    import json
+    h = json.dumps({"format": _FHAT_FORMAT, "version": 1, "Nt": int(Nt), "Nd": int(Nd), "Nm": int(Nm),
+                    "L": int(L_), "Nf": int(L_) // 2 + 1, "ldn": int(ldn), "dtype": "complex128",
+                    "layout": "[Nf][Nd][ldn], padding columns zero"}).encode()
+    if len(h) >= FHAT_HEADER_BYTES:
+        raise ValueError("header too long")
+    return h + b" " * (FHAT_HEADER_BYTES - len(h))
+
+
+def parse_fhat_header(block: bytes) -> dict:
+    """Fields of a header block written by fhat_header (ValueError if it is not one)."""
+    import json
+    if len(block) != FHAT_HEADER_BYTES:
+        raise ValueError("short header")
+    try:
+        h = json.loads(block.decode().rstrip(" "))
+    except (UnicodeDecodeError, json.JSONDecodeError) as e:
+        raise ValueError(f"not an F-hat file: {e}") from None
+    if not isinstance(h, dict) or h.get("format") != _FHAT_FORMAT or h.get("version") != 1:
+        raise ValueError("not an F-hat file (format/version)")
+    for k in ("Nt", "Nd", "Nm", "L", "Nf", "ldn"):
+        if not isinstance(h.get(k), int) or h[k] < 1:
+            raise ValueError(f"bad header field {k}")
+    if h["Nf"] != h["L"] // 2 + 1 or h["ldn"] < h["Nm"] or h["ldn"] % 8 or h["L"] < 2 * h["Nt"] - 1:
+        raise ValueError("inconsistent header sizes")
+    return h
+
+
 def create_operator(F_col, stream=None) -> "Operator":
     """Operator from its first block column F_col[k, r, n] (FP64; host or device)."""
     return Operator(F_col, stream=stream)
@@ -98,11 +132,46 @@ class Operator:
         h = ctypes.c_void_p()
         L.check(lib.fftmv_create_operator(ptr, shape[0], shape[1], shape[2],
                                           _stream_handle(stream, dev), ctypes.byref(h)))
+        self._attach(h)
+
+    def _attach(self, h) -> None:
         self._h = h
         info = L.Info()
-        L.check(lib.fftmv_get_info(self._h, ctypes.byref(info)))
+        L.check(L.lib().fftmv_get_info(self._h, ctypes.byref(info)))
         self.Nt, self.Nd, self.Nm = info.Nt, info.Nd, info.Nm
         self.L, self.Nf, self.ldn, self.device = info.L, info.Nf, info.ldn, info.device
+
+    # -- checkpoint -----------------------------------------------------------
+    def save(self, path, stream=None) -> None:
+        """Write the master F-hat (fftmv_get_fhat) to ``path``: a header block
+        (FHAT_HEADER_BYTES, JSON) and the [Nf][Nd][ldn] complex128 array."""
+        nbytes = self.Nf * self.Nd * self.ldn * 16
+        buf = np.empty(nbytes, dtype=np.uint8)
+        L.check(L.lib().fftmv_get_fhat(self.handle, buf.ctypes.data, nbytes, _stream_handle(stream, None)))
+        with open(path, "wb") as f:
+            f.write(fhat_header(self.Nt, self.Nd, self.Nm, self.L, self.ldn))
+            buf.tofile(f)
+
+    @classmethod
+    def load(cls, path, stream=None) -> "Operator":
+        """Operator from a file written by ``save`` (fftmv_create_from_fhat: no
+        setup FFT), on the current CUDA device."""
+        with open(path, "rb") as f:
+            hdr = parse_fhat_header(f.read(FHAT_HEADER_BYTES))
+            n = hdr["Nf"] * hdr["Nd"] * hdr["ldn"] * 16
+            data = np.fromfile(f, dtype=np.uint8, count=n)
+        if data.size != n:
+            raise ValueError(f"{path}: F-hat truncated ({data.size} of {n} bytes)")
+        h = ctypes.c_void_p()
+        L.check(L.lib().fftmv_create_from_fhat(data.ctypes.data, hdr["Nt"], hdr["Nd"], hdr["Nm"],
+                                               _stream_handle(stream, None), ctypes.byref(h)))
+        op = cls.__new__(cls)
+        op._attach(h)
+        if (op.L, op.ldn) != (hdr["L"], hdr["ldn"]):
+            op.free()
+            raise ValueError(f"{path}: saved with L={hdr['L']}, ldn={hdr['ldn']}; this build uses "
+                             f"L={op.L}, ldn={op.ldn} for Nt={hdr['Nt']}, Nm={hdr['Nm']}")
+        return op
 
     # -- lifetime -----------------------------------------------------------
     def free(self) -> None:
