@@ -169,7 +169,7 @@ class Operator:
         op._attach(h)
         if (op.L, op.ldn) != (hdr["L"], hdr["ldn"]):
             op.free()
-            raise ValueError(f"{path}: saved with L={hdr['L']}, ldn={hdr['ldn']}; this build uses "
+            raise ValueError(f"{path}: saved with L={hdr['L']}, ldn={hdr['ldn']}; this library version uses "
                              f"L={op.L}, ldn={op.ldn} for Nt={hdr['Nt']}, Nm={hdr['Nm']}")
         return op
 
