@@ -385,6 +385,110 @@ __global__ void __launch_bounds__(T) gemv_h_kernel(GemvDesc d) {
   }
 }
 
+// H direction, one right-hand side, bulk-copy pipelined: grid (ceil(ldp /
+// CW), Nf).  Warp 0 (one elected thread) streams the CTA's run of CW packs of
+// RS rows of F-hat_w at a time into a ring of STAGES shared-memory stages with
+// cp.async.bulk (one contiguous copy per row); NCW consumer warps own V packs
+// each (consumer thread tc: packs tc + NC v) and accumulate them over every
+// row with d-hat_w from shared memory, releasing each stage through its
+// "empty" mbarrier.  As the N kernel, bytes stay in flight while the
+// consumers do their double-float arithmetic.
+template <class Kd, int V, int NCW, int RS, int STAGES>
+__global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d) {
+  using Pack = typename Kd::Pack;
+  using Elem = typename Kd::Elem;
+  using Acc = typename Kd::Acc;
+  constexpr int NC = 32 * NCW;
+  constexpr int CW = NC * V;         // packs per row run
+  constexpr int STAGE = RS * CW;     // packs per stage
+  static_assert(Kd::P == 1, "one complex entry per pack");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Pack* stage = reinterpret_cast<Pack*>(smem_raw);
+  Elem* xs = reinterpret_cast<Elem*>(stage + STAGES * STAGE);   // [Nd]
+  uint64_t* full = reinterpret_cast<uint64_t*>(xs + d.Nd);
+  uint64_t* empty = full + STAGES;
+
+  const int w = blockIdx.y;
+  const int ldp = d.ldn;
+  const int p0 = blockIdx.x * CW;
+  const int np = min(CW, ldp - p0);
+  const int nseg = (d.Nd + RS - 1) / RS;
+  const Pack* F = static_cast<const Pack*>(d.F) + (int64_t)w * d.Nd * ldp + p0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCW);
+    }
+    mbar_init_fence();
+  }
+  {
+    const Elem* x = static_cast<const Elem*>(d.x) + (int64_t)w * d.Nd;
+    for (int r = threadIdx.x; r < d.Nd; r += blockDim.x) xs[r] = x[r];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (warp == 0) {  // producer
+    if (lane == 0) {
+      const uint64_t policy = l2_evict_first_policy();
+      const uint32_t bytes = (uint32_t)np * (uint32_t)sizeof(Pack);
+      bool ok = true;
+      int c = 0;
+      for (; c < nseg; ++c) {
+        const int s = c % STAGES;
+        if (c >= STAGES && !mbar_wait(&empty[s], ((c / STAGES) & 1) ^ 1)) {
+          ok = false;
+          break;
+        }
+        const int r0 = c * RS, nr = min(RS, d.Nd - r0);
+        mbar_arrive_expect_tx(&full[s], bytes * (uint32_t)nr);
+        Pack* st = stage + s * STAGE;
+        for (int r = 0; r < nr; ++r)
+          bulk_g2s_hint(st + r * CW, F + (int64_t)(r0 + r) * ldp, bytes, &full[s], policy);
+      }
+      // no copy may outlive the CTA: wait for the last issued stages to land
+      for (int cc = max(0, c - STAGES); cc < c; ++cc)
+        if (!mbar_wait(&full[cc % STAGES], (cc / STAGES) & 1)) ok = false;
+      if (!ok) atomicOr(d.status, kStatusWaitTimeout);
+    }
+    return;
+  }
+
+  // consumers
+  const int tc = threadIdx.x - 32;
+  Acc acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = Kd::zero();
+  for (int c = 0; c < nseg; ++c) {
+    const int s = c % STAGES;
+    if (!mbar_wait(&full[s], (c / STAGES) & 1)) {
+      atomicOr(d.status, kStatusWaitTimeout);
+      break;
+    }
+    const Pack* st = stage + s * STAGE;
+    const int r0 = c * RS, nr = min(RS, d.Nd - r0);
+    // packs past np (last column run only) hold stale shared memory; their
+    // accumulators are never stored
+#pragma unroll
+    for (int r = 0; r < RS; ++r) {
+      if (r < nr) {
+        const Elem xv = xs[r0 + r];
+#pragma unroll
+        for (int v = 0; v < V; ++v) Kd::mac_h(&acc[v], st[r * CW + tc + NC * v], xv);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  const int64_t yo = (int64_t)w * d.ldn + p0;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int p = tc + NC * v;
+    if (p < np) Kd::store(d.y, yo + p, acc[v]);
+  }
+}
+
 // master FP64 F-hat -> stored kind.  The double-float form holds F-hat times
 // the power of two `mul` (exact), which brings its largest entry into [1, 2):
 // FP32 hi/lo pairs have FP32's exponent range, so this keeps every operator
@@ -453,8 +557,43 @@ cudaError_t run_h_kb(const GemvDesc& d, cudaStream_t s) {
 }
 
 // right-hand sides per CTA: up to 8 for FP32 (8-byte entries), 4 otherwise
+// double-float, one right-hand side: the bulk-copy pipeline (V packs per
+// consumer thread, NCW consumer warps, RS rows per stage, STAGES stages)
+#ifndef FFTMV_HPIPE
+#define FFTMV_HPIPE 1
+#endif
+#ifndef FFTMV_HPIPE_V
+#define FFTMV_HPIPE_V 4
+#endif
+#ifndef FFTMV_HPIPE_W
+#define FFTMV_HPIPE_W 4
+#endif
+#ifndef FFTMV_HPIPE_RS
+#define FFTMV_HPIPE_RS 4
+#endif
+#ifndef FFTMV_HPIPE_ST
+#define FFTMV_HPIPE_ST 3
+#endif
+cudaError_t run_h_pipe_df(const GemvDesc& d, cudaStream_t s) {
+  constexpr int V = FFTMV_HPIPE_V, NCW = FFTMV_HPIPE_W, RS = FFTMV_HPIPE_RS, STAGES = FFTMV_HPIPE_ST;
+  constexpr int CW = 32 * NCW * V;
+  auto kernel = gemv_h_pipe_kernel<KindDF, V, NCW, RS, STAGES>;
+  const size_t smem = (size_t)STAGES * RS * CW * sizeof(float4) + (size_t)d.Nd * sizeof(float4) +
+                      2 * STAGES * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((d.ldn + CW - 1) / CW, d.Nf, 1);
+  kernel<<<grid, 32 * (NCW + 1), smem, s>>>(d);
+  return cudaGetLastError();
+}
+
 template <class Kd>
 cudaError_t run_h(const GemvDesc& d, cudaStream_t s) {
+#if FFTMV_HPIPE
+  if constexpr (std::is_same<Kd, KindDF>::value) {
+    if (d.K == 1 && (size_t)d.Nd * sizeof(float4) <= 64 * 1024) return run_h_pipe_df(d, s);
+  }
+#endif
   const int kmax = Kd::P == 2 ? 8 : 4;
   if (d.K >= 8 && kmax >= 8) return run_h_kb<Kd, 8>(d, s);
   if (d.K >= 4) return run_h_kb<Kd, 4>(d, s);
