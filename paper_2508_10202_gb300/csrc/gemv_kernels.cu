@@ -188,12 +188,12 @@ struct KindF32 {
 // them cost ceil(K / KB) passes over F-hat.  Bytes stay in flight while the
 // consumers do their (double-float) arithmetic.
 // ---------------------------------------------------------------------------
-template <class Kd, int R, int KB, int NCW, int STAGES>
+template <class Kd, int R, int KB, int NCW, int STAGES, int V = 1>
 __global__ void __launch_bounds__(32 * (NCW + 1), 2) gemv_n_kernel(GemvDesc d) {
   using Pack = typename Kd::Pack;
   using Acc = typename Kd::Acc;
   constexpr int NC = 32 * NCW;   // consumer threads
-  constexpr int CW = NC;         // packs per row segment
+  constexpr int CW = NC * V;     // packs per row segment (V per consumer thread)
   constexpr int STAGE = (R + KB) * CW;
   static_assert(R * KB <= NC, "one consumer thread per output");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -262,17 +262,21 @@ __global__ void __launch_bounds__(32 * (NCW + 1), 2) gemv_n_kernel(GemvDesc d) {
       break;
     }
     const Pack* st = stage + s * STAGE;
-    if (tc < ldp - c * CW) {
-      // rows r >= nr and right-hand sides k >= nbk (last blocks only) hold
-      // stale shared memory; their accumulators are never stored
-      Pack xv[KB];
 #pragma unroll
-      for (int k = 0; k < KB; ++k) xv[k] = st[(R + k) * CW + tc];
+    for (int v = 0; v < V; ++v) {
+      const int q = tc + NC * v;   // pack of the segment
+      if (q < ldp - c * CW) {
+        // rows r >= nr and right-hand sides k >= nbk (last blocks only) hold
+        // stale shared memory; their accumulators are never stored
+        Pack xv[KB];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const Pack f = st[r * CW + tc];
+        for (int k = 0; k < KB; ++k) xv[k] = st[(R + k) * CW + q];
 #pragma unroll
-        for (int k = 0; k < KB; ++k) Kd::mac_n(acc[r][k], f, xv[k]);
+        for (int r = 0; r < R; ++r) {
+          const Pack f = st[r * CW + q];
+#pragma unroll
+          for (int k = 0; k < KB; ++k) Kd::mac_n(acc[r][k], f, xv[k]);
+        }
       }
     }
     __syncwarp();
@@ -510,17 +514,32 @@ __global__ void convert_f32_kernel(const double2* __restrict__ in, float2* __res
 }
 
 // N, one right-hand side: rows per CTA, consumer warps, pipeline stages.
-// Double-float takes 4 rows and 4 consumer warps (55 KB of stages, four CTAs
-// per SM: 2.30 ms against 2.45 ms for 8 x 8 at the paper shape); FP32 and FP64
-// keep 8 rows and 8 warps, their best.
+// Double-float: FFTMV_NDF_* below (2.45 ms with 8 rows and 8 warps); FP32 and
+// FP64 keep 8 rows and 8 warps, their best.
 constexpr int kNR = 8, kNW = 8, kNS = 3;
-constexpr int kNR_DF = 4, kNW_DF = 4;
+// double-float: 2 rows, 4 consumer warps with 2 packs each per segment (4 KB
+// row runs), 3 stages: 2.26 ms at the paper shape against 2.29 for 4 rows and
+// one pack (2 KB runs), 2.34 for 4 rows and two packs, 2.33 / 2.69 for 4 rows
+// and four packs with 2 / 3 stages, 2.27 for 2 rows and four packs, 2.39 for
+// one row and four packs
+#ifndef FFTMV_NDF_R
+#define FFTMV_NDF_R 2
+#endif
+#ifndef FFTMV_NDF_W
+#define FFTMV_NDF_W 4
+#endif
+#ifndef FFTMV_NDF_ST
+#define FFTMV_NDF_ST 3
+#endif
+#ifndef FFTMV_NDF_V
+#define FFTMV_NDF_V 2
+#endif
 constexpr int kHV = 2, kHT = 256, kHU = 4;   // H: packs per thread, threads, rows in flight
 
-template <class Kd, int R, int KB, int NCW, int STAGES>
+template <class Kd, int R, int KB, int NCW, int STAGES, int V = 1>
 cudaError_t run_n_cfg(const GemvDesc& d, cudaStream_t s) {
-  auto kernel = gemv_n_kernel<Kd, R, KB, NCW, STAGES>;
-  const size_t smem = (size_t)STAGES * (R + KB) * (32 * NCW) * sizeof(typename Kd::Pack) +
+  auto kernel = gemv_n_kernel<Kd, R, KB, NCW, STAGES, V>;
+  const size_t smem = (size_t)STAGES * (R + KB) * (32 * NCW * V) * sizeof(typename Kd::Pack) +
                       2 * STAGES * sizeof(uint64_t) + (size_t)NCW * R * KB * sizeof(typename Kd::Acc);
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -531,7 +550,8 @@ cudaError_t run_n_cfg(const GemvDesc& d, cudaStream_t s) {
 
 template <class Kd>
 cudaError_t run_n(const GemvDesc& d, cudaStream_t s) {
-  if constexpr (std::is_same<Kd, KindDF>::value) return run_n_cfg<Kd, kNR_DF, 1, kNW_DF, kNS>(d, s);
+  if constexpr (std::is_same<Kd, KindDF>::value)
+    return run_n_cfg<Kd, FFTMV_NDF_R, 1, FFTMV_NDF_W, FFTMV_NDF_ST, FFTMV_NDF_V>(d, s);
   else return run_n_cfg<Kd, kNR, 1, kNW, kNS>(d, s);
 }
 
