@@ -69,9 +69,9 @@ VARIANTS = {
 # input), the forward FFT, the block matvec and the inverse FFT (plus one
 # cudaMemsetAsync of the range check's K words)
 KERNELS_PER_MATVEC = 4
-# mean DRAM bytes per launch of gemv_n/gemv_h<KindDF> at the paper shape (ncu dram__bytes
-# read + write on Nm=2000, 3.238e9 and 3.212e9 B, scaled by 5 in Nm)
-GEMV_DF_TRAFFIC = 16.12e9
+# mean DRAM bytes per launch of gemv_n_kernel / gemv_h_pipe_kernel <KindDF> at the paper
+# shape (ncu dram__bytes read + write on Nm=2000, 3.239e9 and 3.214e9 B, scaled by 5 in Nm)
+GEMV_DF_TRAFFIC = 16.13e9
 # DRAM bytes (read + write) per K=64 bf16x2 call at the paper shape, per kernel, from
 # ncu captures at Nm=2000 (profiles/fft_L2000_Nm2000_full.md, tc_gemm_k64_Nm2000_full.md)
 # scaled by 5 in Nm where the traffic grows with Nm; the parts that do not (F*'s B planes
@@ -771,7 +771,7 @@ def main(args) -> None:
     # scaled x5 to the full operator (profiles/gemv_df_paper_shape_Nm2000_full.md)
     traffic = GEMV_DF_TRAFFIC if (Nt, Nd, Nm) == (NT, ND, NM) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "gemv_n_kernel<KindDF> (F) / gemv_h_kernel<KindDF> (F*)",
+                "traffic": traffic, "kernel": "gemv_n_kernel<KindDF> (F) / gemv_h_pipe_kernel<KindDF> (F*)",
                 "bytes_per_launch": ab, "gemv_ms_F": tf[1] / nf, "gemv_ms_Fstar": ta[1] / na,
                 "frac_F": ab / (tf[1] / nf * 1e-3) / 1e9 / peak, "frac_Fstar": ab / (ta[1] / na * 1e-3) / 1e9 / peak,
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
