@@ -405,7 +405,6 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d)
   constexpr int NC = 32 * NCW;
   constexpr int CW = NC * V;         // packs per row run
   constexpr int STAGE = RS * CW;     // packs per stage
-  static_assert(Kd::P == 1, "one complex entry per pack");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Pack* stage = reinterpret_cast<Pack*>(smem_raw);
   Elem* xs = reinterpret_cast<Elem*>(stage + STAGES * STAGE);   // [Nd]
@@ -413,7 +412,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d)
   uint64_t* empty = full + STAGES;
 
   const int w = blockIdx.y;
-  const int ldp = d.ldn;
+  const int ldp = d.ldn / Kd::P;     // packs per row
   const int p0 = blockIdx.x * CW;
   const int np = min(CW, ldp - p0);
   const int nseg = (d.Nd + RS - 1) / RS;
@@ -461,9 +460,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d)
 
   // consumers
   const int tc = threadIdx.x - 32;
-  Acc acc[V];
+  Acc acc[V][Kd::P];
 #pragma unroll
-  for (int v = 0; v < V; ++v) acc[v] = Kd::zero();
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int e = 0; e < Kd::P; ++e) acc[v][e] = Kd::zero();
   for (int c = 0; c < nseg; ++c) {
     const int s = c % STAGES;
     if (!mbar_wait(&full[s], (c / STAGES) & 1)) {
@@ -479,17 +480,20 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d)
       if (r < nr) {
         const Elem xv = xs[r0 + r];
 #pragma unroll
-        for (int v = 0; v < V; ++v) Kd::mac_h(&acc[v], st[r * CW + tc + NC * v], xv);
+        for (int v = 0; v < V; ++v) Kd::mac_h(acc[v], st[r * CW + tc + NC * v], xv);
       }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
-  const int64_t yo = (int64_t)w * d.ldn + p0;
+  const int64_t yo = (int64_t)w * d.ldn + (int64_t)p0 * Kd::P;
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int p = tc + NC * v;
-    if (p < np) Kd::store(d.y, yo + p, acc[v]);
+    if (p < np) {
+#pragma unroll
+      for (int e = 0; e < Kd::P; ++e) Kd::store(d.y, yo + (int64_t)p * Kd::P + e, acc[v][e]);
+    }
   }
 }
 
@@ -577,8 +581,9 @@ cudaError_t run_h_kb(const GemvDesc& d, cudaStream_t s) {
 }
 
 // right-hand sides per CTA: up to 8 for FP32 (8-byte entries), 4 otherwise
-// double-float, one right-hand side: the bulk-copy pipeline (V packs per
-// consumer thread, NCW consumer warps, RS rows per stage, STAGES stages)
+// one right-hand side in double-float or FP32: the bulk-copy pipeline (V
+// packs per consumer thread, NCW consumer warps, RS rows per stage, STAGES
+// stages)
 #ifndef FFTMV_HPIPE
 #define FFTMV_HPIPE 1
 #endif
@@ -594,15 +599,21 @@ cudaError_t run_h_kb(const GemvDesc& d, cudaStream_t s) {
 #ifndef FFTMV_HPIPE_ST
 #define FFTMV_HPIPE_ST 3
 #endif
-cudaError_t run_h_pipe_df(const GemvDesc& d, cudaStream_t s) {
+#ifndef FFTMV_HPIPE_F32
+#define FFTMV_HPIPE_F32 1
+#endif
+template <class Kd>
+cudaError_t run_h_pipe(const GemvDesc& d, cudaStream_t s) {
   constexpr int V = FFTMV_HPIPE_V, NCW = FFTMV_HPIPE_W, RS = FFTMV_HPIPE_RS, STAGES = FFTMV_HPIPE_ST;
   constexpr int CW = 32 * NCW * V;
-  auto kernel = gemv_h_pipe_kernel<KindDF, V, NCW, RS, STAGES>;
-  const size_t smem = (size_t)STAGES * RS * CW * sizeof(float4) + (size_t)d.Nd * sizeof(float4) +
+  using Pack = typename Kd::Pack;
+  using Elem = typename Kd::Elem;
+  auto kernel = gemv_h_pipe_kernel<Kd, V, NCW, RS, STAGES>;
+  const size_t smem = (size_t)STAGES * RS * CW * sizeof(Pack) + (size_t)d.Nd * sizeof(Elem) +
                       2 * STAGES * sizeof(uint64_t);
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((d.ldn + CW - 1) / CW, d.Nf, 1);
+  dim3 grid((d.ldn / Kd::P + CW - 1) / CW, d.Nf, 1);
   kernel<<<grid, 32 * (NCW + 1), smem, s>>>(d);
   return cudaGetLastError();
 }
@@ -610,8 +621,10 @@ cudaError_t run_h_pipe_df(const GemvDesc& d, cudaStream_t s) {
 template <class Kd>
 cudaError_t run_h(const GemvDesc& d, cudaStream_t s) {
 #if FFTMV_HPIPE
-  if constexpr (std::is_same<Kd, KindDF>::value) {
-    if (d.K == 1 && (size_t)d.Nd * sizeof(float4) <= 64 * 1024) return run_h_pipe_df(d, s);
+  if constexpr (!std::is_same<Kd, KindF64>::value) {
+    if (d.K == 1 && (size_t)d.Nd * sizeof(typename Kd::Elem) <= 64 * 1024 &&
+        (FFTMV_HPIPE_F32 || std::is_same<Kd, KindDF>::value))
+      return run_h_pipe<Kd>(d, s);
   }
 #endif
   const int kmax = Kd::P == 2 ? 8 : 4;
