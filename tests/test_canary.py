@@ -35,6 +35,13 @@ CASES = [
     (256, 5, 37, 3, "sssss", "native", "native", np.float32),
     (128, 6, 70, 70, "sssss", "bf16x2", "native", np.float32),
     (100, 9, 40, 5, "sssss", "f16x2", "native", np.float32),
+    # one right-hand side: the pipelined block matvecs, with ragged row
+    # segments (Nd not a multiple of the rows per stage or per CTA) and
+    # ragged column runs (a second, partial 512-pack run; a single short one)
+    (64, 7, 99, 1, "ddddd", "f64x2f32", "f64x2f32", np.float64),
+    (50, 5, 1300, 1, "sssss", "native", "native", np.float32),
+    (1000, 3, 9, 1, "ddddd", "f64x2f32", "f64x2f32", np.float64),
+    (128, 9, 600, 1, "ddddd", "f64x2f32", "f64x2f32", np.float32),
 ]
 
 
