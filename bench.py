@@ -12,7 +12,9 @@ value      matvecs/s over all ranks with inputs resident in HBM, device time
            is all-FP64-class (every phase FP64, the block matvec in the
            double-float FP32 hi/lo mode, relative L2 <= 1e-12 to the oracle).
 e2e        the same metric through the public API with host (pinned) buffers,
-           host<->device copies inside the timed region.
+           host<->device copies inside the timed region; consecutive steps
+           alternate between two streams, so one step's copies (and FFTs)
+           overlap the other's kernels.
 roofline   the block-matvec kernels (about 90 % of a step): algorithmic bytes
            per launch (F-hat at its stored width + input + output vectors of
            one matvec) over their mean CUDA-event duration, against the
@@ -27,6 +29,11 @@ rel_err    every error here is the relative L2 distance, over whole outputs,
            That path's parity with the oracle, at these sizes and in this
            launch configuration, is checked by tests/test_fullsize.py; the
            GPU arm itself never runs the oracle.
+multi_rhs  64 right-hand sides per call on the tensor cores (bf16 or FP16
+           hi/lo), F and F*, with each kernel's time and DRAM bytes.
+small      the plain FP64 Nt=64, Nd=8, Nm=32 workload: microseconds per matvec
+           for the fused single launch and for the three-kernel path.
+served     the four-operator served mix: capacity and p50/p99 latency.
 cpu_baseline  the CPU oracle's FFT path on the whole operator (F-hat built
            and applied in blocks of rows), a few steps on all host cores.
 
