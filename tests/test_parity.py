@@ -140,6 +140,34 @@ def test_sizes(torch_cuda, Nt, Nd, Nm, prec, mode, fft_mode):
     op.free()
 
 
+# --- one right-hand side: the pipelined block matvecs -----------------------
+# (the F* kernel keeps d-hat in shared memory up to 64 KB: Nd = 4096 double-float
+# or 8192 FP32 entries; one more row takes the unpipelined kernel)
+
+@pytest.mark.parametrize("Nt,Nd,Nm", [(1, 1, 1), (5, 3, 7), (12, 5, 17), (100, 13, 257), (300, 17, 513),
+                                      (16, 4096, 8), (16, 4097, 8), (8, 8192, 3)])
+@pytest.mark.parametrize("prec,mode,fft_mode", [("ddddd", "f64x2f32", "f64x2f32"), ("sssss", "native", "native"),
+                                                ("dssdd", "native", "f64x2f32")])
+def test_one_rhs_block_matvecs(torch_cuda, Nt, Nd, Nm, prec, mode, fft_mode):
+    torch = torch_cuda
+    Fcol, m, d = make_case(Nt, Nd, Nm, K=1, seed=Nt + Nd + Nm)
+    op = gpu_op(torch, Fcol)
+    op.set_precision("F", prec, mode, fft_mode)
+    op.set_precision("F*", prec, mode, fft_mode)
+    y, x = run_both(torch, op, m[0], d[0])
+    # the block matvec sums n = Nm (F) or Nd (F*) products per frequency in its
+    # own arithmetic (unit roundoff u: 2^-24 FP32, 2^-48 double-float); with
+    # random signs the outputs are about sqrt(n) times smaller than the sum of
+    # the magnitudes, so relative to the output norm the rounding grows like
+    # n u: the bar is the larger of the stated tolerance and 4 n u
+    u = 2.0 ** -24 if prec[2] == "s" else 2.0 ** -48
+    base = TOL64 if prec == "ddddd" else TOL32
+    assert oracle.rel_l2(y, oracle.matvec_direct(Fcol, m[0])) <= max(base, 4 * Nm * u)
+    assert oracle.rel_l2(x, oracle.rmatvec_direct(Fcol, d[0])) <= max(base, 4 * Nd * u)
+    assert op.device_status() == 0
+    op.free()
+
+
 # --- the lengths with FFT kernels of their own (L = 128, 256, 512, 1000, 2000) --
 # In native FP64 a transform whose grid would cover fewer SMs than the GPU has
 # runs with fewer channel pairs per CTA on the runtime-length kernel, so K = 3
