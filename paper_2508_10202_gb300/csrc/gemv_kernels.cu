@@ -522,10 +522,11 @@ __global__ void convert_f32_kernel(const double2* __restrict__ in, float2* __res
 // FP64 keep 8 rows and 8 warps, their best.
 constexpr int kNR = 8, kNW = 8, kNS = 3;
 // double-float: 2 rows, 4 consumer warps with 2 packs each per segment (4 KB
-// row runs), 3 stages: 2.26 ms at the paper shape against 2.29 for 4 rows and
-// one pack (2 KB runs), 2.34 for 4 rows and two packs, 2.33 / 2.69 for 4 rows
-// and four packs with 2 / 3 stages, 2.27 for 2 rows and four packs, 2.39 for
-// one row and four packs
+// row runs), 2 stages: 2.25 ms at the paper shape; with 3 stages 2.26, with 4
+// stages 2.43; 2.29 for 4 rows and one pack (2 KB runs), 2.34 for 4 rows and
+// two packs, 2.33 / 2.69 for 4 rows and four packs with 2 / 3 stages, 2.27 for
+// 2 rows and four packs, 2.39 for one row and four packs, 2.30 with 2 consumer
+// warps
 #ifndef FFTMV_NDF_R
 #define FFTMV_NDF_R 2
 #endif
@@ -533,7 +534,7 @@ constexpr int kNR = 8, kNW = 8, kNS = 3;
 #define FFTMV_NDF_W 4
 #endif
 #ifndef FFTMV_NDF_ST
-#define FFTMV_NDF_ST 3
+#define FFTMV_NDF_ST 2
 #endif
 #ifndef FFTMV_NDF_V
 #define FFTMV_NDF_V 2
