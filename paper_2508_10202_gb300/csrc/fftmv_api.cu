@@ -839,6 +839,7 @@ int fftmv_workspace_bytes(const fftmv_op* op, int which, int64_t K, size_t* out)
   if (rc) return rc;
   if (which != FFTMV_FORWARD && which != FFTMV_ADJOINT) return fail(FFTMV_EINVAL, "which=%d is not F/F*", which);
   if (K < 0 || !out) return fail(FFTMV_EINVAL, "bad K or null output");
+  DeviceGuard dg(op->device);   // whether a call is fused depends on the operator's device
   const CallPlan c = plan_call(op, which, K);
   *out = c.in_hat + c.out_hat;
   return FFTMV_OK;

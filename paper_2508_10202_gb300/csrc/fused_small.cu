@@ -206,30 +206,32 @@ cudaError_t fused_launch(const FusedDesc& d, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, kern, d);
 }
 
-// whether the device schedules 16-CTA clusters of the largest fused kernel
-// (checked once per device)
-bool cluster16_ok() {
+// whether the current device schedules CL-CTA clusters of the largest fused
+// kernel (checked once per device and cluster size)
+template <int CL>
+bool clusters_ok() {
   static int cache[64];
   static std::once_flag once[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
   std::call_once(once[dev], [&] {
-    auto kern = fused_small_kernel<double, 4, 256, 16>;
-    constexpr size_t smem = fused_smem_bytes<256, 4, 16>();
+    auto kern = fused_small_kernel<double, 4, 256, CL>;
+    constexpr size_t smem = fused_smem_bytes<256, 4, CL>();
     int n = 0;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(16, 1, 1);
+    cfg.gridDim = dim3(CL, 1, 1);
     cfg.blockDim = dim3(kFusedThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.x = CL;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const bool ok = prep(kern, smem) == cudaSuccess &&
-                    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+                    (CL <= 8 || cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                                    cudaSuccess) &&
                     cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0;
     cudaGetLastError();
     cache[dev] = ok ? 1 : 0;
@@ -248,7 +250,7 @@ cudaError_t fused_launch_np(const FusedDesc& d, cudaStream_t s) {
 template <typename Tio, int L>
 cudaError_t fused_launch_cl(const FusedDesc& d, cudaStream_t s) {
 #if FFTMV_FUSED_CL16
-  if (cluster16_ok()) return fused_launch_np<Tio, L, 16>(d, s);
+  if (clusters_ok<16>()) return fused_launch_np<Tio, L, 16>(d, s);
 #endif
   return fused_launch_np<Tio, L, 8>(d, s);
 }
@@ -256,7 +258,10 @@ cudaError_t fused_launch_cl(const FusedDesc& d, cudaStream_t s) {
 }  // namespace
 
 bool fused_small_fits(int64_t L, int64_t Cin, int64_t Cout) {
-  return (L == 128 || L == 256) && Cin >= 1 && Cout >= 1 && Cin <= kFusedMaxChannels && Cout <= kFusedMaxChannels;
+  // the sizes one cluster takes, on a device that schedules 8-CTA clusters of
+  // the kernel (else every call takes the three-kernel path)
+  return (L == 128 || L == 256) && Cin >= 1 && Cout >= 1 && Cin <= kFusedMaxChannels && Cout <= kFusedMaxChannels &&
+         clusters_ok<8>();
 }
 
 cudaError_t launch_fused_small(const FusedDesc& d, cudaStream_t s) {
