@@ -25,7 +25,7 @@ def torch_cuda():
 # (Nt, Nd, Nm, K): L = 128 or 256; channel counts from 1 to the 64 one cluster
 # holds, odd ones, and both directions' widest side
 CASES = [(64, 8, 32, 1), (64, 8, 32, 3), (64, 1, 1, 2), (64, 64, 64, 2), (128, 5, 37, 2), (127, 33, 2, 1),
-         (61, 17, 64, 4), (128, 64, 1, 1)]
+         (61, 17, 64, 4), (128, 64, 1, 1), (64, 8, 32, 200)]   # the last: more clusters than fit at once
 
 
 @pytest.mark.parametrize("Nt,Nd,Nm,K", CASES)
