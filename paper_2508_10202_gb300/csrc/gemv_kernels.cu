@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(T) gemv_h_kernel(GemvDesc d) {
 // row with d-hat_w from shared memory, releasing each stage through its
 // "empty" mbarrier.  As the N kernel, bytes stay in flight while the
 // consumers do their double-float arithmetic.
-template <class Kd, int V, int NCW, int RS, int STAGES>
+template <class Kd, int V, int NCW, int RS, int STAGES, int KB>
 __global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d) {
   using Pack = typename Kd::Pack;
   using Elem = typename Kd::Elem;
@@ -407,11 +407,13 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d)
   constexpr int STAGE = RS * CW;     // packs per stage
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Pack* stage = reinterpret_cast<Pack*>(smem_raw);
-  Elem* xs = reinterpret_cast<Elem*>(stage + STAGES * STAGE);   // [Nd]
-  uint64_t* full = reinterpret_cast<uint64_t*>(xs + d.Nd);
+  Elem* xs = reinterpret_cast<Elem*>(stage + STAGES * STAGE);   // [KB][Nd]
+  uint64_t* full = reinterpret_cast<uint64_t*>(xs + KB * d.Nd);
   uint64_t* empty = full + STAGES;
 
   const int w = blockIdx.y;
+  const int b0 = blockIdx.z * KB;
+  const int nb = min(KB, d.K - b0);
   const int ldp = d.ldn / Kd::P;     // packs per row
   const int p0 = blockIdx.x * CW;
   const int np = min(CW, ldp - p0);
@@ -425,9 +427,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d)
     }
     mbar_init_fence();
   }
-  {
-    const Elem* x = static_cast<const Elem*>(d.x) + (int64_t)w * d.Nd;
-    for (int r = threadIdx.x; r < d.Nd; r += blockDim.x) xs[r] = x[r];
+  for (int i = threadIdx.x; i < KB * d.Nd; i += blockDim.x) {
+    const int k = i / d.Nd, r = i - k * d.Nd;
+    const Elem* x = static_cast<const Elem*>(d.x) + (b0 + k) * d.x_ld_b + (int64_t)w * d.Nd;
+    if (k < nb) xs[i] = x[r];
+    else xs[i] = Elem{};   // right-hand sides past K: zeros, results not stored
   }
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -460,11 +464,13 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d)
 
   // consumers
   const int tc = threadIdx.x - 32;
-  Acc acc[V][Kd::P];
+  Acc acc[V][KB][Kd::P];
 #pragma unroll
   for (int v = 0; v < V; ++v)
 #pragma unroll
-    for (int e = 0; e < Kd::P; ++e) acc[v][e] = Kd::zero();
+    for (int k = 0; k < KB; ++k)
+#pragma unroll
+      for (int e = 0; e < Kd::P; ++e) acc[v][k][e] = Kd::zero();
   for (int c = 0; c < nseg; ++c) {
     const int s = c % STAGES;
     if (!mbar_wait(&full[s], (c / STAGES) & 1)) {
@@ -478,21 +484,31 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) gemv_h_pipe_kernel(GemvDesc d)
 #pragma unroll
     for (int r = 0; r < RS; ++r) {
       if (r < nr) {
-        const Elem xv = xs[r0 + r];
+        Pack f[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) Kd::mac_h(acc[v], st[r * CW + tc + NC * v], xv);
+        for (int v = 0; v < V; ++v) f[v] = st[r * CW + tc + NC * v];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const Elem xv = xs[k * d.Nd + r0 + r];
+#pragma unroll
+          for (int v = 0; v < V; ++v) Kd::mac_h(acc[v][k], f[v], xv);
+        }
       }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
-  const int64_t yo = (int64_t)w * d.ldn + (int64_t)p0 * Kd::P;
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const int p = tc + NC * v;
-    if (p < np) {
+  for (int k = 0; k < KB; ++k) {
+    if (k >= nb) break;
+    const int64_t yo = (b0 + k) * d.y_ld_b + (int64_t)w * d.ldn + (int64_t)p0 * Kd::P;
 #pragma unroll
-      for (int e = 0; e < Kd::P; ++e) Kd::store(d.y, yo + (int64_t)p * Kd::P + e, acc[v][e]);
+    for (int v = 0; v < V; ++v) {
+      const int p = tc + NC * v;
+      if (p < np) {
+#pragma unroll
+        for (int e = 0; e < Kd::P; ++e) Kd::store(d.y, yo + (int64_t)p * Kd::P + e, acc[v][k][e]);
+      }
     }
   }
 }
@@ -603,18 +619,21 @@ cudaError_t run_h_kb(const GemvDesc& d, cudaStream_t s) {
 #ifndef FFTMV_HPIPE_F32
 #define FFTMV_HPIPE_F32 1
 #endif
-template <class Kd>
+#ifndef FFTMV_HPIPE_MULTI
+#define FFTMV_HPIPE_MULTI 1
+#endif
+template <class Kd, int KB, int V>
 cudaError_t run_h_pipe(const GemvDesc& d, cudaStream_t s) {
-  constexpr int V = FFTMV_HPIPE_V, NCW = FFTMV_HPIPE_W, RS = FFTMV_HPIPE_RS, STAGES = FFTMV_HPIPE_ST;
+  constexpr int NCW = FFTMV_HPIPE_W, RS = FFTMV_HPIPE_RS, STAGES = FFTMV_HPIPE_ST;
   constexpr int CW = 32 * NCW * V;
   using Pack = typename Kd::Pack;
   using Elem = typename Kd::Elem;
-  auto kernel = gemv_h_pipe_kernel<Kd, V, NCW, RS, STAGES>;
-  const size_t smem = (size_t)STAGES * RS * CW * sizeof(Pack) + (size_t)d.Nd * sizeof(Elem) +
+  auto kernel = gemv_h_pipe_kernel<Kd, V, NCW, RS, STAGES, KB>;
+  const size_t smem = (size_t)STAGES * RS * CW * sizeof(Pack) + (size_t)KB * d.Nd * sizeof(Elem) +
                       2 * STAGES * sizeof(uint64_t);
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((d.ldn / Kd::P + CW - 1) / CW, d.Nf, 1);
+  dim3 grid((d.ldn / Kd::P + CW - 1) / CW, d.Nf, (d.K + KB - 1) / KB);
   kernel<<<grid, 32 * (NCW + 1), smem, s>>>(d);
   return cudaGetLastError();
 }
@@ -623,9 +642,18 @@ template <class Kd>
 cudaError_t run_h(const GemvDesc& d, cudaStream_t s) {
 #if FFTMV_HPIPE
   if constexpr (!std::is_same<Kd, KindF64>::value) {
-    if (d.K == 1 && (size_t)d.Nd * sizeof(typename Kd::Elem) <= 64 * 1024 &&
-        (FFTMV_HPIPE_F32 || std::is_same<Kd, KindDF>::value))
-      return run_h_pipe<Kd>(d, s);
+    // one right-hand side: V = FFTMV_HPIPE_V packs per thread; several: up to 8
+    // (FP32) or 4 (double-float) per pass over F-hat with 2 packs per thread,
+    // so the accumulators stay in registers
+    const size_t el = sizeof(typename Kd::Elem);
+    if (d.K == 1 && (size_t)d.Nd * el <= 64 * 1024 && (FFTMV_HPIPE_F32 || std::is_same<Kd, KindDF>::value))
+      return run_h_pipe<Kd, 1, FFTMV_HPIPE_V>(d, s);
+    if (FFTMV_HPIPE_MULTI && d.K > 1) {
+      constexpr int kmaxp = Kd::P == 2 ? 8 : 4;
+      if (d.K >= kmaxp && (size_t)kmaxp * d.Nd * el <= 64 * 1024) return run_h_pipe<Kd, kmaxp, 2>(d, s);
+      if (d.K >= 4 && (size_t)4 * d.Nd * el <= 64 * 1024) return run_h_pipe<Kd, 4, 2>(d, s);
+      if ((size_t)2 * d.Nd * el <= 64 * 1024) return run_h_pipe<Kd, 2, 2>(d, s);
+    }
   }
 #endif
   const int kmax = Kd::P == 2 ? 8 : 4;
