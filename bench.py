@@ -33,6 +33,9 @@ multi_rhs  64 right-hand sides per call on the tensor cores (bf16 or FP16
            hi/lo), F and F*, with each kernel's time and DRAM bytes.
 small      the plain FP64 Nt=64, Nd=8, Nm=32 workload: microseconds per matvec
            for the fused single launch and for the three-kernel path.
+autograd   the differentiable adjoint Nt=500, Nd=200, Nm=5000 in FP32: loss +
+           gradient (F forward, F* backward) per second, its HBM fraction and
+           the gradient's error.
 served     the four-operator served mix: capacity and p50/p99 latency.
 cpu_baseline  the CPU oracle's FFT path on the whole operator (F-hat built
            and applied in blocks of rows), a few steps on all host cores.
@@ -562,6 +565,62 @@ def bench_hessian(torch, op, Fcol, stream, batch: int = 64, batches: int = 4) ->
             "rel_err_8_columns": rel_diff(cols[:8], ref)}
 
 
+def bench_autograd(torch, dev, iters: int = 20) -> dict:
+    """The differentiable-adjoint workload Nt=500, Nd=200, Nm=5000 in FP32: one
+    loss + gradient of 1/2 ||F m - d||^2 is one F (forward) and one F* (backward,
+    through autograd), each reading F-hat once (FP32, 4.0e9 B).  The gradient is
+    compared with F*(F m - d) through the plain FP64 path."""
+    import numpy as np
+
+    import synth
+    from paper_2508_10202_gb300 import Operator
+    from paper_2508_10202_gb300.autograd import toeplitz_matvec
+    Nt, Nd, Nm = 500, 200, 5000
+    Fcol = synth.block_column(Nt, Nd, Nm, seed=0)
+    op = Operator(Fcol)
+    del Fcol
+    m_true = torch.from_numpy(synth.vectors(synth.TAG_M, Nt, Nm, seed=0)[0]).to(dev)
+    op.set_precision("F", "ddddd", "native", "native")
+    d_clean = op.matvec(m_true)
+    noise = torch.from_numpy(synth.vectors(synth.TAG_NOISE, Nt, Nd, seed=0)[0]).to(dev)
+    d = (d_clean + 0.01 * d_clean.norm() / (Nt * Nd) ** 0.5 * noise).float()
+    m = torch.from_numpy(synth.vectors(synth.TAG_M, Nt, Nm, seed=1)[0]).to(dev).float().requires_grad_(True)
+    for w in ("F", "F*"):
+        op.set_precision(w, "sssss", "native", "native")
+
+    def step():
+        m.grad = None
+        r = toeplitz_matvec(op, m) - d
+        loss = 0.5 * (r * r).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        step()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / iters
+    g = m.grad.double()
+    for w in ("F", "F*"):
+        op.set_precision(w, "ddddd", "native", "native")
+    md = m.detach().double()
+    g64 = op.rmatvec(op.matvec(md) - d.double())
+    op.free()
+    fhat = (Nt + 1) * Nd * Nm * 8
+    ab = 2 * (fhat + Nt * Nm * 4 + Nt * Nd * 4)
+    peak, _ = load_peaks()
+    return {"workload": "differentiable adjoint Nt=500 Nd=200 Nm=5000, FP32 (sssss), loss + gradient",
+            "ms_per_loss_grad": ms, "loss_grads_per_s": 1e3 / ms,
+            "algorithmic_bytes": ab, "hbm_frac": ab / (ms * 1e-3) / 1e9 / peak,
+            "rel_err_grad": rel_diff(g, g64),
+            "note": "the time includes the residual and loss arithmetic in PyTorch between the two matvecs"}
+
+
 # the served mix: four resident operators (Nt, Nd, Nm), blocks N(0,1) in float32
 SERVE_OPS = {"op128": (128, 16, 1000), "op256": (256, 64, 4000), "op500": (500, 100, 10000),
              "op1000": (1000, 200, 8000)}
@@ -845,8 +904,10 @@ def main(args) -> None:
         hess = bench_hessian(torch, op, Fcol, stream)
 
     small = None
+    autograd = None
     if rank == 0 and not args.no_variants:
         small = bench_small(torch, dev)
+        autograd = bench_autograd(torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -873,7 +934,8 @@ def main(args) -> None:
                         "how": "relative L2 over the whole outputs against the plain FP64 path (native FP64 FMA) "
                                "on the same inputs; that path's parity with the oracle is tests/test_fullsize.py"},
             "roofline": roofline, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, "variants": variants,
-            "multi_rhs": multi, "hessian": hess, "small": small, "pareto": pareto, "paper_shape": paper_shape,
+            "multi_rhs": multi, "hessian": hess, "small": small, "autograd": autograd, "pareto": pareto,
+            "paper_shape": paper_shape,
             "served": served,
             "served_p50_ms": served["load_0.9"]["p50_ms"] if served else None,
             "served_p99_ms": served["load_0.9"]["p99_ms"] if served else None,
