@@ -474,7 +474,8 @@ def bench_small(torch, dev, calls: int = 2000) -> dict:
     latency-bound, so it reports microseconds per call, issued directly and as
     a replayed CUDA graph of caller-scratch calls, for the fused single-launch
     path (one 16-CTA cluster per call, the default at this size) and for the
-    three-kernel path; a roofline fraction means nothing at this size."""
+    three-kernel path, then the same in all-FP32 precision;
+    a roofline fraction means nothing at this size."""
     import synth
     from paper_2508_10202_gb300 import Operator
     Nt, Nd, Nm = 64, 8, 32
@@ -525,11 +526,20 @@ def bench_small(torch, dev, calls: int = 2000) -> dict:
     us_direct, us_graph = run()
     op.set_fusion(False)
     us_direct3, us_graph3 = run()
+    # the same workload with every phase in FP32 (FP64 inputs and outputs)
+    op.set_precision("F", "sssss")
+    op.set_precision("F*", "sssss")
+    op.set_fusion(True)
+    f32_direct, f32_graph = run()
+    op.set_fusion(False)
+    f32_direct3, f32_graph3 = run()
     op.free()
     return {"workload": "plain FP64, Nt=64 Nd=8 Nm=32, F and F* alternating", "precision": "ddddd/native",
             "us_per_matvec_direct": us_direct, "us_per_matvec_graph": us_graph,
             "matvec_s_graph": 1e6 / us_graph, "path": "fused: one cluster launch per call",
             "three_kernel_path": {"us_per_matvec_direct": us_direct3, "us_per_matvec_graph": us_graph3},
+            "fp32": {"precision": "sssss/native", "us_per_matvec_direct": f32_direct, "us_per_matvec_graph": f32_graph,
+                     "three_kernel_path": {"us_per_matvec_direct": f32_direct3, "us_per_matvec_graph": f32_graph3}},
             "roofline": "not meaningful: launch- and latency-bound"}
 
 

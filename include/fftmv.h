@@ -184,15 +184,16 @@ int fftmv_set_scratch_limit(fftmv_op* op, size_t bytes);
 
 /* Fused small-operator calls (Section 2.4's five phases in one launch; on by
  * default).  A call whose precision is all FP64 with native arithmetic
- * (pad, FFT, GEMV, IFFT, unpad = F64; gemv_mode = fft_mode = NATIVE), whose FFT
- * length L is 128 or 256 and whose input and output channel counts are both
- * at most 64 runs as one launch per call: one cluster of 8 CTAs per right-hand
- * side keeps both spectra in shared memory (exchanged through distributed
- * shared memory) and takes no scratch from the pool.  Its results equal the
- * three-kernel path's up to the rounding order of the FP64 sums; with timing
- * on, its whole duration is reported as the first phase.  enable = 0 sends
- * every call through the three-kernel path.  Errors: EINVAL / ESTATE for a bad
- * handle. */
+ * (pad, FFT, GEMV, IFFT, unpad = F64; gemv_mode = fft_mode = NATIVE) or all
+ * FP32 (every phase F32, gemv_mode = NATIVE; any fft_mode), whose FFT length L
+ * is 128 or 256 and whose input and output channel counts are both at most 64
+ * runs as one launch per call: one thread-block cluster per right-hand side
+ * (16 CTAs where the device schedules them, else 8) keeps both spectra in
+ * shared memory (exchanged through distributed shared memory) and takes no
+ * scratch from the pool.  Its results equal the three-kernel path's up to the
+ * rounding order of the sums; with timing on, its whole duration is reported
+ * as the first phase.  enable = 0 sends every call through the three-kernel
+ * path.  Errors: EINVAL / ESTATE for a bad handle. */
 int fftmv_set_fusion(fftmv_op* op, int enable);
 
 /* F m (which = FFTMV_FORWARD) or F* d (FFTMV_ADJOINT) with caller-supplied

@@ -138,7 +138,7 @@ struct fftmv_op {
   int64_t calls[2] = {};
   size_t scratch_limit = 0;  // 0: kCallScratchBudget
   int fexp = 0;              // range exponent of F-hat: max |Re, Im| / 2^fexp in [1, 2)
-  bool fusion = true;        // small all-FP64 calls as one fused launch (fftmv_set_fusion)
+  bool fusion = true;        // small all-FP64 or all-FP32 calls as one fused launch (fftmv_set_fusion)
 };
 
 namespace {
@@ -242,13 +242,21 @@ struct CallPlan {
   bool fused;              // one fused launch (fused_small.cu), no spectra in scratch
 };
 
-// all five phases in native FP64 on an operator whose spectra fit one cluster
+// every phase in FP32 with the FP32 copy of F-hat (the FFT mode applies to
+// FP64 transforms only, so it does not matter here)
+bool all_f32(const fftmv_op* op, const fftmv_precision& p) {
+  return p.pad == FFTMV_F32 && p.fft == FFTMV_F32 && p.gemv == FFTMV_F32 && p.ifft == FFTMV_F32 &&
+         p.unpad == FFTMV_F32 && p.gemv_mode == FFTMV_GEMV_NATIVE && op->fhat32 != nullptr;
+}
+
+// all five phases in native FP64, or all in FP32, on an operator whose
+// spectra fit one cluster
 bool fused_call(const fftmv_op* op, int which) {
   const fftmv_precision& p = op->prec[which];
   const bool fwd = which == FFTMV_FORWARD;
-  return op->fusion && p.pad == FFTMV_F64 && p.fft == FFTMV_F64 && p.gemv == FFTMV_F64 && p.ifft == FFTMV_F64 &&
-         p.unpad == FFTMV_F64 && p.gemv_mode == FFTMV_GEMV_NATIVE && p.fft_mode == FFTMV_GEMV_NATIVE &&
-         fused_small_fits(op->L, fwd ? op->Nm : op->Nd, fwd ? op->Nd : op->Nm);
+  const bool f64 = p.pad == FFTMV_F64 && p.fft == FFTMV_F64 && p.gemv == FFTMV_F64 && p.ifft == FFTMV_F64 &&
+                   p.unpad == FFTMV_F64 && p.gemv_mode == FFTMV_GEMV_NATIVE && p.fft_mode == FFTMV_GEMV_NATIVE;
+  return op->fusion && (f64 || all_f32(op, p)) && fused_small_fits(op->L, fwd ? op->Nm : op->Nd, fwd ? op->Nd : op->Nm);
 }
 
 CallPlan plan_call(const fftmv_op* op, int which, int64_t K) {
@@ -291,10 +299,11 @@ cudaError_t launch_phases(const fftmv_op* op, int which, const CallPlan& c, cons
   if (ev) cudaEventRecord(ev[0], s);
   if (c.fused) {   // the whole call is one launch; its time is reported as the first phase
     FusedDesc u{};
+    u.f32 = all_f32(op, p);
     u.x = x;
     u.y = y;
-    u.F = op->fhat64;
-    u.tw = op->tw64;
+    u.F = u.f32 ? (const void*)op->fhat32 : (const void*)op->fhat64;
+    u.tw = u.f32 ? (const void*)op->tw32 : (const void*)op->tw64;
     u.Nt = (int)op->Nt;
     u.L = (int)op->L;
     u.Nd = (int)op->Nd;

@@ -209,22 +209,27 @@ cudaError_t launch_rhs_scales(const void* x, bool x_f32, int K, int64_t n, int N
                               float* inv, cudaStream_t s);
 size_t tc_smem_bytes(int N);
 
-// Fused single-launch matvec of a small operator, all phases FP64 (fused_small.cu):
-// x[b][t][Cin] -> y[b][t][Cout] (FP64 or FP32 I/O), F-hat [Nf][Nd][ldn] FP64.
+// Fused single-launch matvec of a small operator, all phases FP64 or all FP32
+// (fused_small.cu, fused_small_f32.cu): x[b][t][Cin] -> y[b][t][Cout] (FP64 or
+// FP32 I/O), F-hat [Nf][Nd][ldn] in the phases' precision.
 struct FusedDesc {
   const void* x;
   void* y;
-  const double2* F;        // master F-hat
-  const double2* tw;       // twiddles exp(-2 pi i j / L), j < L
+  const void* F;           // F-hat: the master (double2), or its FP32 copy (float2) when f32
+  const void* tw;          // twiddles exp(-2 pi i j / L), j < L, in the same type
   int Nt, L, Nd, ldn;
   int Cin, Cout, K;
   int adjoint;             // 0: F (Cin = Nm, Cout = Nd), 1: F* (Cin = Nd, Cout = Nm)
   int io_f32;
+  int f32;                 // every phase in FP32 (else every phase in FP64)
   int64_t x_ld_b, y_ld_b;  // element strides between right-hand sides
   double inv_L;
 };
 bool fused_small_fits(int64_t L, int64_t Cin, int64_t Cout);
 cudaError_t launch_fused_small(const FusedDesc& d, cudaStream_t s);
+// d.f32 set, sizes checked by the caller; cl16: the device schedules 16-CTA
+// clusters of the largest FP64 fused kernel (and so of every FP32 one)
+cudaError_t launch_fused_small_f32(const FusedDesc& d, bool cl16, cudaStream_t s);
 
 cudaError_t launch_rfft_fwd(const FwdDesc& d, bool in_f32, int prec, cudaStream_t s);
 cudaError_t launch_irfft_inv(const InvDesc& d, int prec, bool out_f32, cudaStream_t s);

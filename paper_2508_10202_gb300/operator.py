@@ -220,7 +220,7 @@ class Operator:
         return out.value
 
     def set_fusion(self, enable: bool = True) -> None:
-        """Small all-FP64 calls as one fused launch (fftmv_set_fusion; on by default)."""
+        """Small all-FP64 and all-FP32 calls as one fused launch (fftmv_set_fusion; on by default)."""
         L.check(L.lib().fftmv_set_fusion(self.handle, int(bool(enable))))
 
     def set_scratch_limit(self, nbytes: int = 0) -> None:

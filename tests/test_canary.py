@@ -24,11 +24,13 @@ def torch_cuda():
     return torch
 
 
-# (Nt, Nd, Nm, K, prec, mode, fft_mode, io): the fused small path, the
-# three-kernel FP64 path, the double-float in-place FFTs (L = 2000), FP32,
-# and the tensor cores with a ragged last chunk
+# (Nt, Nd, Nm, K, prec, mode, fft_mode, io): the fused small paths (FP64 and
+# FP32), the three-kernel FP64 path, the double-float in-place FFTs
+# (L = 2000), FP32, and the tensor cores with a ragged last chunk
 CASES = [
     (64, 8, 32, 2, "ddddd", "native", "native", np.float64),
+    (64, 8, 32, 2, "sssss", "native", "native", np.float64),
+    (128, 33, 2, 3, "sssss", "native", "native", np.float32),
     (50, 7, 99, 3, "ddddd", "native", "native", np.float64),
     (1000, 4, 9, 2, "ddddd", "f64x2f32", "f64x2f32", np.float64),
     (1000, 4, 9, 2, "ddddd", "f64x2f32", "f64x2f32", np.float32),
