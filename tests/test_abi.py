@@ -95,3 +95,15 @@ def test_create_without_gpu_reports_cuda_error(lib):
     h = ctypes.c_void_p()
     assert lib.fftmv_create_operator(x.ctypes.data, 2, 2, 2, None, ctypes.byref(h)) == -4
     assert h.value is None
+
+
+def test_no_fallback_without_the_library(monkeypatch, tmp_path):
+    # the package has no CPU path: with the shared library missing, creating
+    # an operator raises ImportError instead of computing anything
+    from paper_2508_10202_gb300 import Operator, _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libfftmv.so"))
+    with pytest.raises(ImportError, match="no fallback"):
+        _lib.lib()
+    with pytest.raises(ImportError, match="no fallback"):
+        Operator(np.zeros((2, 1, 1)))
