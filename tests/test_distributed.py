@@ -63,7 +63,9 @@ def _worker(rank, world, pr, port):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,pr", [(2, 1), (4, 2)])   # row reduce; broadcast + both reductions
+# 1 x 2: the row reduction; 2 x 1: the column reduction with one-rank row
+# groups; 2 x 2: the broadcast and both reductions
+@pytest.mark.parametrize("world,pr", [(2, 1), (2, 2), (4, 2)])
 def test_sharded_operator_gloo(world, pr):
     mp.spawn(_worker, args=(world, pr, _free_port()), nprocs=world, join=True)
 
