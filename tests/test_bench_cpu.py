@@ -40,3 +40,23 @@ def test_reference_arm_line():
     # the timed steps are the whole operator: value and ms_per_step agree
     assert abs(line["value"] - 2e3 / line["ms_per_step"]) <= 1e-6 * line["value"]
     assert np.isfinite(line["value"])
+
+
+def test_reference_arm_under_two_ranks():
+    # launched as the multi-GPU bench is (torch.distributed.run, 2 ranks): rank
+    # 0 alone times the oracle and prints the one line, the other exits 0
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--Nt", "16", "--Nd", "5", "--Nm", "12",
+                        "--steps", "2", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["steps"] == 2
+    assert line["value"] > 0
