@@ -60,3 +60,31 @@ def test_reference_arm_under_two_ranks():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["steps"] == 2
     assert line["value"] > 0
+
+
+def _rank_reduce_worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    out[rank] = (bench.max_over_ranks(1.5 + rank, world), bench.sum_over_ranks(1.5 + rank, world))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_rank_reductions_gloo():
+    # the GPU arm's time is the maximum over ranks and its units the sum, on
+    # every rank (gloo on CPU here; NCCL on the GPU machine)
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    world = 3
+    with mp.get_context("spawn").Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_rank_reduce_worker, args=(world, port, out), nprocs=world, join=True)
+        got = dict(out)
+    assert got == {r: (3.5, 7.5) for r in range(world)}
+    import bench
+    assert bench.max_over_ranks(2.0, 1) == 2.0 and bench.sum_over_ranks(2.0, 1) == 2.0
