@@ -107,3 +107,19 @@ def test_no_fallback_without_the_library(monkeypatch, tmp_path):
         _lib.lib()
     with pytest.raises(ImportError, match="no fallback"):
         Operator(np.zeros((2, 1, 1)))
+
+
+def test_binding_rejects_bad_block_columns_before_any_call():
+    # the Python binding checks dtype, rank and layout itself (no GPU needed)
+    import torch
+    from paper_2508_10202_gb300 import Operator
+    with pytest.raises(ValueError, match="float64"):
+        Operator(np.zeros((2, 3, 4), dtype=np.float32))      # FP32 block column
+    with pytest.raises(ValueError, match="float64"):
+        Operator(np.zeros((2, 3)))                            # not (Nt, Nd, Nm)
+    with pytest.raises(TypeError, match="not supported"):
+        Operator(np.zeros((2, 3, 4), dtype=np.int64))
+    with pytest.raises(ValueError, match="contiguous"):
+        Operator(np.zeros((4, 3, 2)).transpose(2, 1, 0))
+    with pytest.raises(ValueError, match="contiguous"):
+        Operator(torch.zeros((4, 3, 2), dtype=torch.float64).permute(2, 1, 0))
